@@ -1,0 +1,335 @@
+"""Throughput benchmark: FWBF decoding of EG(1023,781) frames on GB300.
+
+One step = one pass of the whole decoding path over one batch: int8
+quantisation of the float channel values, then FWBF decoding of every frame
+(initialisation, syndrome, metric of Eq. 1, block arg-max, flips, stop test)
+through the C ABI.  Inputs are synthetic (seeded random information bits,
+systematic encoding, BPSK over AWGN) and already resident in HBM; they are far
+larger than L2 (4.3 GB of float32 per step), so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the CPU oracle on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "decoded info Gb/s on 1 GB300 at matched FER: learned+batched vs plain FWBF"
+SM_COUNT = 152
+INT_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+WORKLOAD = dict(code="eg1023", ebn0_db=4.0, frames=1 << 20, max_iter=100, seg_len=31, alpha=1.5)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=WORKLOAD["frames"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(frames):
+    w = WORKLOAD
+    return {
+        "workload": f"EG(1023,781) FWBF int8, {frames} frames/step at Eb/N0 {w['ebn0_db']} dB "
+                    f"(a point of the 3.0-5.0 dB sweep), random info bits, p={w['seg_len']}, "
+                    f"K_max={w['max_iter']}, alpha={w['alpha']}",
+        "code": "EG(2,2^5) type-I cyclic (1023,781)",
+        "frames_per_step": frames,
+        "ebn0_db": w["ebn0_db"],
+        "seg_len": w["seg_len"],
+        "max_iter": w["max_iter"],
+        "alpha": w["alpha"],
+        "l2": "inputs larger than L2 (no flush)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_ops(iters, max_iter, E, N, B):
+    """Integer work the method defines for a batch: per frame one
+    initialisation (2E + N: the weights and the syndrome) and, per flip pass,
+    2E + N + B (syndrome and metric over every edge, one compare per bit, one
+    flip test per block).  A frame that fails runs max_iter passes."""
+    import torch
+
+    passes = torch.where(iters < 0, torch.full_like(iters, max_iter), iters).to(torch.int64).sum().item()
+    return iters.numel() * (2 * E + N) + passes * (2 * E + N + B)
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the machine's host cores: each step decodes
+    a bounded sample of the workload's frames (host-generated, same recipe)."""
+    import numpy as np
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1206_3362_gb300.inputs import Encoder, bpsk_awgn, make_code, random_codewords
+
+    w = WORKLOAD
+    h = make_code(w["code"])
+    enc = Encoder(h)
+    sample = 1024
+    _, c = random_codewords(enc, sample, seed=2024)
+    q = oracle.quantize(bpsk_awgn(c, w["ebn0_db"], enc.rate, seed=2024))
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.fwbf_i8_threaded(h, w["seg_len"], q[:threads], w["max_iter"], w["alpha"], threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fwbf_i8_threaded(h, w["seg_len"], q, w["max_iter"], w["alpha"], threads=threads)
+    dt = time.perf_counter() - t0
+    value = sample * args.steps * enc.K / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gb/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+        "data": "synthetic", "config": workload_config(sample),
+        "cpu_baseline": {"value": value, "unit": "Gb/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} frames per step of the same workload, host-generated"},
+        "e2e": {"value": value, "unit": "Gb/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1206_3362_gb300 import fwbf
+    from paper_1206_3362_gb300.inputs import Encoder, make_code
+    from paper_1206_3362_gb300.inputs.channel import bpsk_awgn_torch, random_codewords_torch
+
+    w = WORKLOAD
+    F = args.frames
+    h = make_code(w["code"])
+    enc = Encoder(h)
+    E, N = h.nnz, h.N
+    _, c = random_codewords_torch(enc, F, seed=1000 + rank, device=dev)
+    y = bpsk_awgn_torch(c, w["ebn0_db"], enc.rate, seed=1000 + rank).contiguous()
+    code = fwbf.Code.from_parity_check(h, w["seg_len"])
+    B = code.info.n_blocks
+    q = torch.empty((F, N), dtype=torch.int8, device=dev)
+    bits, iters = code.outputs(F, dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fwbf.fwbf_quantize(y, q, stream)
+        fwbf.fwbf_decode(code.handle, q, w["max_iter"], w["alpha"], bits, iters, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps; events around every decode launch for the roofline
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record(stream)
+    for k in range(args.steps):
+        fwbf.fwbf_quantize(y, q, stream)
+        ev[k][0].record(stream)
+        fwbf.fwbf_decode(code.handle, q, w["max_iter"], w["alpha"], bits, iters, stream)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = t_start.elapsed_time(t_end)
+    dec_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    assert fwbf.fwbf_last_status(stream) == 0
+
+    info_bits = F * enc.K * world * args.steps
+    value = info_bits / (ms / 1e3) / 1e9
+    it = iters
+    fail = (it < 0).float().mean().item()
+    conv_iters = it[it >= 0].float().mean().item() if (it >= 0).any() else float("nan")
+    ops = algorithmic_ops(it, w["max_iter"], E, N, B)
+    peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = ops / (dec_ms / 1e3) / 1e12
+    # frame error rate against the transmitted codewords
+    zb = bits.view(torch.uint8)
+    fe = 0
+    for s0 in range(0, F, 1 << 16):
+        z = ((zb[s0:s0 + (1 << 16)].unsqueeze(-1) >> torch.arange(8, device=dev, dtype=torch.uint8)) & 1)
+        z = z.reshape(z.shape[0], -1)[:, :N]
+        fe += (z != c[s0:s0 + (1 << 16)]).any(dim=1).sum().item()
+    fer = fe / F
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "Gb/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": workload_config(F), "fer": fer, "failed_frames": fail,
+        "avg_passes_converged": conv_iters,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "fwbf_decode_i8_kernel", "decode_ms": dec_ms,
+                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (derived)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clock_info,
+    }
+
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = e2e(args, fwbf, code, y, w, F, enc, dev, stream)
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(fwbf, h, enc, q, bits, iters, w)
+    if rank == 0:
+        print(json.dumps(result))
+    code.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e(args, fwbf, code, y, w, F, enc, dev, stream):
+    """Same metric through the public API with host buffers: every step copies
+    the float channel values from pinned host memory, quantises, decodes and
+    copies the decisions and pass counts back."""
+    import torch
+
+    y_host = y.cpu().pin_memory()
+    bits_host = torch.empty((F, code.words), dtype=torch.int32).pin_memory()
+    iters_host = torch.empty(F, dtype=torch.int32).pin_memory()
+    yd = torch.empty_like(y)
+    qd = torch.empty((F, code.N), dtype=torch.int8, device=dev)
+    bd, idd = code.outputs(F, dev)
+
+    def step():
+        yd.copy_(y_host, non_blocking=True)
+        fwbf.fwbf_quantize(yd, qd, stream)
+        fwbf.fwbf_decode(code.handle, qd, w["max_iter"], w["alpha"], bd, idd, stream)
+        bits_host.copy_(bd, non_blocking=True)
+        iters_host.copy_(idd, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 5))
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    return {"value": F * enc.K * steps / (ms / 1e3) / 1e9, "unit": "Gb/s",
+            "h2d_bytes_per_step": y_host.numel() * 4,
+            "d2h_bytes_per_step": bits_host.numel() * 4 + iters_host.numel() * 4,
+            "steps": steps, "ms_per_step": ms / steps}
+
+
+def cpu_baseline(fwbf, h, enc, q, bits, iters, w):
+    """The CPU oracle on the host cores, on a bounded sample of the same
+    frames; also reports how many sampled frames the GPU matched bit-exactly."""
+    import numpy as np
+
+    import oracle
+
+    sample = 4096
+    qs = q[:sample].cpu().numpy()
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    bo, io, used = oracle.fwbf_i8_threaded(h, w["seg_len"], qs, w["max_iter"], w["alpha"], threads=threads)
+    dt = time.perf_counter() - t0
+    gb = bits[:sample].cpu().numpy().view(np.uint32)
+    gi = iters[:sample].cpu().numpy()
+    match = int(((gi == io) & (gb == bo).all(axis=1)).sum())
+    return {"value": sample * enc.K / dt / 1e9, "unit": "Gb/s", "cores": used, "kind": "oracle",
+            "sample": f"first {sample} frames of the timed batch, decoded once ({dt:.1f} s wall)",
+            "parity_sample_match": f"{match}/{sample}"}
+
+
+if __name__ == "__main__":
+    main()

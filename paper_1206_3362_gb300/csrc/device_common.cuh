@@ -1,0 +1,109 @@
+// Device helpers shared by the decoding kernels: division by small runtime
+// constants, circulant index arithmetic, and the bulk-copy (TMA) staging of
+// the code tables into shared memory with a bounded mbarrier wait.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fwbf {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// x / d for x < 65536 and 1 <= d <= 65535, with magic = ceil(2^32 / d) (d > 1)
+__device__ __forceinline__ uint32_t div_small(uint32_t x, uint32_t d, uint32_t magic) {
+    return d == 1 ? x : __umulhi(x, magic);
+}
+
+// bit of check (block row entry ent, offset i):  C*Z + ((i + t) mod Z)
+__device__ __forceinline__ uint32_t circ_index(uint32_t ent, uint32_t i, uint32_t Z) {
+    uint32_t j = i + (ent & 0xffffu);
+    j = j >= Z ? j - Z : j;
+    return (ent >> 16) * Z + j;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy (TMA, 1-D): 16-byte aligned addresses, size % 16 == 0
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for phase `parity` of the barrier for at most limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+constexpr uint32_t kBulkChunk = 65536;
+
+// Stages `words` uint32 of the global table into shared memory with bulk
+// copies, the whole CTA waiting on one mbarrier.  Returns false for every
+// thread of the CTA if the copy did not complete within the wait limit (the
+// caller then records the timeout and leaves).
+__device__ __forceinline__ bool stage_table(uint32_t *dst, const uint32_t *src, uint32_t words, uint64_t *bar,
+                                            int *flag) {
+    const uint32_t bytes = words * 4u;
+    if (threadIdx.x == 0) {
+        *flag = 0;
+        mbar_init(bar, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += kBulkChunk) {
+            uint32_t n = bytes - off < kBulkChunk ? bytes - off : kBulkChunk;
+            bulk_g2s(reinterpret_cast<char *>(dst) + off, reinterpret_cast<const char *>(src) + off, n, bar);
+        }
+    }
+    bool ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (!ok) {
+        // let the copies in flight land before the CTA leaves
+        mbar_wait_bounded(bar, 0, kWaitLimitNs);
+        atomicOr(flag, 1);
+    }
+    __syncthreads();
+    return *flag == 0;
+}
+
+__device__ __forceinline__ int warp_sum(int v) { return __reduce_add_sync(FULL, v); }
+
+}  // namespace fwbf

@@ -1,0 +1,237 @@
+"""ctypes binding of libfwbf.so with the C ABI's entry-point names.
+
+Argument marshalling only: every step of decoding runs in the library's CUDA
+kernels.  Tensors are PyTorch CUDA tensors (used for device memory and
+streams); the calls pass ``tensor.data_ptr()`` and the current stream.  There
+is no fallback: if the library is missing or a call fails, an exception is
+raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfwbf.so")
+
+FWBF_OK = 0
+FWBF_EINVAL = -1
+FWBF_ENOMEM = -2
+FWBF_ECUDA = -3
+FWBF_EUNSUPPORTED = -4
+FWBF_ETIMEOUT = -5
+
+
+class FwbfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class CodeInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("Z", ctypes.c_int32), ("dv_max", ctypes.c_int32), ("dc_max", ctypes.c_int32),
+                ("seg_len", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("table_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libfwbf.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    sig = {
+        "fwbf_code_create": ([i32, i32, i64, P, P, i32, ctypes.POINTER(P)], ctypes.c_int),
+        "fwbf_destroy": ([P], ctypes.c_int),
+        "fwbf_code_query": ([P, ctypes.POINTER(CodeInfo)], ctypes.c_int),
+        "fwbf_quantize": ([P, P, i64, P], ctypes.c_int),
+        "fwbf_decode": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
+        "fwbf_decode_f32": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
+        "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
+        "fwbf_last_status": ([P], ctypes.c_int),
+        "fwbf_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "fwbf_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (argt, rest) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = argt
+        fn.restype = rest
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != FWBF_OK:
+        lib = load_library()
+        raise FwbfError(rc, f"{lib.fwbf_strerror(rc).decode()}: {lib.fwbf_last_error().decode()}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def fwbf_code_create(N: int, M: int, row_idx, col_idx, seg_len: int) -> ctypes.c_void_p:
+    lib = load_library()
+    rows = np.ascontiguousarray(row_idx, dtype=np.int32)
+    cols = np.ascontiguousarray(col_idx, dtype=np.int32)
+    if rows.shape != cols.shape:
+        raise ValueError("row_idx and col_idx differ in length")
+    h = ctypes.c_void_p()
+    _check(lib.fwbf_code_create(int(N), int(M), rows.size, rows.ctypes.data_as(ctypes.c_void_p),
+                                cols.ctypes.data_as(ctypes.c_void_p), int(seg_len), ctypes.byref(h)))
+    return h
+
+
+def fwbf_destroy(code) -> None:
+    _check(load_library().fwbf_destroy(code))
+
+
+def fwbf_code_query(code) -> CodeInfo:
+    info = CodeInfo()
+    _check(load_library().fwbf_code_query(code, ctypes.byref(info)))
+    return info
+
+
+def fwbf_quantize(y, q, stream=None) -> None:
+    import torch
+
+    if y.numel() != q.numel():
+        raise ValueError("y and q differ in size")
+    _check(load_library().fwbf_quantize(_dev(y, torch.float32, "y"), _dev(q, torch.int8, "q"), y.numel(),
+                                        _stream(stream)))
+
+
+def _frames(y, N):
+    if y.dim() != 2 or y.shape[1] != N:
+        raise ValueError(f"y must have shape [n_frames, {N}]")
+    return y.shape[0]
+
+
+def fwbf_decode(code, y, max_iter: int, alpha: float, out_bits, out_iters, stream=None) -> None:
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y, info.N)
+    _check(load_library().fwbf_decode(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
+                                      _dev(out_bits, torch.int32, "out_bits"),
+                                      _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
+
+
+def fwbf_decode_f32(code, y, max_iter: int, alpha: float, out_bits, out_iters, stream=None) -> None:
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y, info.N)
+    _check(load_library().fwbf_decode_f32(code, _dev(y, torch.float32, "y"), F, int(max_iter), float(alpha),
+                                          _dev(out_bits, torch.int32, "out_bits"),
+                                          _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
+
+
+def fwbf_metric_f32(code, y, alpha: float, out_E, stream=None) -> None:
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y, info.N)
+    _check(load_library().fwbf_metric_f32(code, _dev(y, torch.float32, "y"), F, float(alpha),
+                                          _dev(out_E, torch.float32, "out_E"), _stream(stream)))
+
+
+def fwbf_last_status(stream=None) -> int:
+    return load_library().fwbf_last_status(_stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Code:
+    """Owns a code handle; decode helpers allocate the outputs."""
+
+    def __init__(self, N: int, M: int, row_idx, col_idx, seg_len: int):
+        self.handle = fwbf_code_create(N, M, row_idx, col_idx, seg_len)
+        self.info = fwbf_code_query(self.handle)
+        self.N, self.M = N, M
+        self.words = (N + 31) // 32
+
+    @classmethod
+    def from_parity_check(cls, h, seg_len: int) -> "Code":
+        return cls(h.N, h.M, h.rows, h.cols, seg_len)
+
+    def close(self):
+        if self.handle:
+            fwbf_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, F: int, device="cuda"):
+        import torch
+
+        return (torch.empty((F, self.words), dtype=torch.int32, device=device),
+                torch.empty(F, dtype=torch.int32, device=device))
+
+    def decode(self, y, max_iter: int, alpha: float, stream=None):
+        bits, iters = self.outputs(y.shape[0], y.device)
+        fwbf_decode(self.handle, y, max_iter, alpha, bits, iters, stream)
+        return bits, iters
+
+    def decode_f32(self, y, max_iter: int, alpha: float, stream=None):
+        bits, iters = self.outputs(y.shape[0], y.device)
+        fwbf_decode_f32(self.handle, y, max_iter, alpha, bits, iters, stream)
+        return bits, iters
+
+    def metric_f32(self, y, alpha: float, stream=None):
+        import torch
+
+        out = torch.empty_like(y)
+        fwbf_metric_f32(self.handle, y, alpha, out, stream)
+        return out
+
+
+def quantize(y, stream=None):
+    import torch
+
+    q = torch.empty(y.shape, dtype=torch.int8, device=y.device)
+    fwbf_quantize(y, q, stream)
+    return q

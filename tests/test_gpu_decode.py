@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+int8 path: decisions and pass counts bit-exact on every frame.  float32 path:
+first-pass metric within 1e-5 relative to the magnitude of its terms, and
+decisions identical on every frame whose decision margins exceed that bound.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_3362_gb300.inputs import Encoder, bpsk_awgn, make_code, random_codewords
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def fwbf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1206_3362_gb300 import fwbf as mod
+
+    return mod
+
+
+def gpu_decode(fwbf, h, p, q, max_iter, alpha):
+    with fwbf.Code.from_parity_check(h, p) as code:
+        qd = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+        bits, iters = code.decode(qd, max_iter, alpha)
+        torch.cuda.synchronize()
+        assert fwbf.fwbf_last_status() == 0
+        return bits.cpu().numpy().view(np.uint32), iters.cpu().numpy()
+
+
+def frames(key, F, ebn0, seed, zero=False):
+    h = make_code(key)
+    enc = Encoder(h)
+    if zero:
+        c = np.zeros((F, h.N), dtype=np.uint8)
+    else:
+        _, c = random_codewords(enc, F, seed=seed)
+    y = bpsk_awgn(c, ebn0, enc.rate, seed=seed)
+    return h, c, y
+
+
+def assert_same(fwbf, h, p, q, max_iter, alpha, threads=None):
+    b_gpu, i_gpu = gpu_decode(fwbf, h, p, q, max_iter, alpha)
+    b_ref, i_ref, _ = oracle.fwbf_i8_threaded(h, p, q, max_iter, alpha, threads=threads)
+    bad = np.flatnonzero((i_gpu != i_ref) | (b_gpu != b_ref).any(axis=1))
+    assert bad.size == 0, f"{bad.size} frames differ, first {bad[:5]}: gpu {i_gpu[bad[:5]]} oracle {i_ref[bad[:5]]}"
+    return i_ref
+
+
+# ---------------------------------------------------------------------------
+# quantiser
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("count,offset", [(0, 0), (1, 0), (3, 1), (4097, 0), (4097, 3), (1 << 20, 0)])
+def test_quantize_matches_oracle(fwbf, count, offset):
+    rng = np.random.default_rng(count + offset)
+    y = (rng.standard_normal(count + offset) * 4).astype(np.float32)
+    special = np.array([0.0, -0.0, 1 / 32, -1 / 32, 3 / 32, 5 / 32, 7.96875, 8.0, -8.0, 1e30,
+                        np.nan, np.inf, -np.inf, -1e-40], dtype=np.float32)
+    y[: min(y.size, special.size)] = special[: min(y.size, special.size)]
+    yd = torch.from_numpy(y).cuda()[offset:]
+    q = torch.empty(count, dtype=torch.int8, device="cuda")
+    fwbf.fwbf_quantize(yd, q)
+    torch.cuda.synchronize()
+    assert np.array_equal(q.cpu().numpy(), oracle.quantize(y[offset:]))
+
+
+# ---------------------------------------------------------------------------
+# int8 decoder, bit-exact
+# ---------------------------------------------------------------------------
+
+def test_small_random_code_workload(fwbf):
+    """(3,6)-regular N=504, all-zero codeword, 4 dB, 1000 frames, K_max = 50,
+    p = 32 (ragged last block of 24)."""
+    h, c, y = frames("rand504", 1000, 4.0, seed=1, zero=True)
+    q = oracle.quantize(y)
+    assert_same(fwbf, h, 32, q, 50, 1.5)
+
+
+@pytest.mark.parametrize("ebn0", [3.0, 4.0, 5.0])
+@pytest.mark.parametrize("p", [31, 93])
+def test_eg1023(fwbf, ebn0, p):
+    h, c, y = frames("eg1023", 384, ebn0, seed=3)
+    assert_same(fwbf, h, p, oracle.quantize(y), 100, 1.5)
+
+
+@pytest.mark.parametrize("p", [1, 16, 100, 255])
+@pytest.mark.parametrize("max_iter", [1, 5, 10, 50])
+def test_eg255_block_lengths_and_kmax(fwbf, p, max_iter):
+    h, c, y = frames("eg255", 300, 3.0, seed=p * 100 + max_iter)
+    assert_same(fwbf, h, p, oracle.quantize(y), max_iter, 1.0)
+
+
+@pytest.mark.parametrize("key,p", [("rand2016", 32), ("qc8192", 64), ("eg4095", 63)])
+def test_other_codes(fwbf, key, p):
+    h, c, y = frames(key, 64, 4.0, seed=5)
+    assert_same(fwbf, h, p, oracle.quantize(y), 30, 1.5)
+
+
+def test_circulant_structure_detected(fwbf):
+    for key, Z in (("eg1023", 1023), ("qc8192", 256), ("rand504", 1)):
+        h = make_code(key)
+        with fwbf.Code.from_parity_check(h, 31) as code:
+            assert code.info.Z == Z
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.5, 3.0, 63.75])
+def test_alpha_range(fwbf, alpha):
+    h, c, y = frames("eg255", 200, 3.5, seed=8)
+    assert_same(fwbf, h, 16, oracle.quantize(y), 20, alpha)
+
+
+def test_edge_frames(fwbf):
+    """Saturated values, zeros, constant magnitudes (every metric tie), and
+    frames that never converge."""
+    h = make_code("eg255")
+    rng = np.random.default_rng(0)
+    q = []
+    q.append(np.full(h.N, 127, dtype=np.int8))
+    q.append(np.full(h.N, -127, dtype=np.int8))
+    q.append(np.zeros(h.N, dtype=np.int8))
+    q.append(np.where(rng.random(h.N) < 0.5, 16, -16).astype(np.int8))        # heavy ties
+    q.append(np.where(rng.random(h.N) < 0.1, -127, 127).astype(np.int8))
+    q.append(rng.integers(-127, 128, h.N).astype(np.int8))                     # noise only
+    q.append(rng.integers(-2, 3, h.N).astype(np.int8))                         # tiny magnitudes
+    for _ in range(25):
+        q.append(rng.integers(-127, 128, h.N).astype(np.int8))
+    q = np.stack(q)
+    for p in (1, 5, 255):
+        i = assert_same(fwbf, h, p, q, 25, 1.0)
+    assert (i < 0).any()
+
+
+def test_frame_counts_ragged(fwbf):
+    """n_frames 0, 1 and counts that leave warps, CTAs and the last 16-byte
+    chunk of the buffer partly filled."""
+    h, c, y = frames("rand504", 777, 3.0, seed=12)
+    q = oracle.quantize(y)
+    for F in (1, 2, 33, 777):
+        assert_same(fwbf, h, 32, q[:F], 20, 1.5)
+    with fwbf.Code.from_parity_check(h, 32) as code:
+        bits, iters = code.outputs(0)
+        fwbf.fwbf_decode(code.handle, torch.empty((0, h.N), dtype=torch.int8, device="cuda"), 20, 1.5, bits, iters)
+        torch.cuda.synchronize()
+
+
+def test_odd_length_frames_unaligned_offsets(fwbf):
+    """N = 255 bytes per frame: every frame starts at a different offset inside
+    its 16-byte chunk."""
+    h, c, y = frames("eg255", 257, 3.0, seed=13)
+    assert_same(fwbf, h, 16, oracle.quantize(y), 15, 1.0)
+
+
+def test_all_weight_two_errors_eg15(fwbf):
+    """Brute force on the (15,7) code: every error pattern of weight <= 2 on a
+    noiseless frame, for every block length."""
+    h = make_code("eg15")
+    pats = [()] + [(i,) for i in range(15)] + [(i, j) for i in range(15) for j in range(i + 1, 15)]
+    q = np.full((len(pats), 15), 16, dtype=np.int8)
+    for f, pat in enumerate(pats):
+        q[f, list(pat)] = -16
+    for p in range(1, 16):
+        i = assert_same(fwbf, h, p, q, 10, 1.0)
+        assert (i >= 0).all()
+
+
+def test_hand_traced_frame(fwbf):
+    with open(os.path.join(GOLD, "eg15_trace.json")) as f:
+        g = json.load(f)
+    h = make_code("eg15")
+    q = np.array(g["q"], dtype=np.int8)[None]
+    bits, iters = gpu_decode(fwbf, h, g["p"], q, g["max_iter"], g["alpha"])
+    assert iters[0] == g["iters"]
+    assert oracle.unpack_bits(bits, 15)[0].tolist() == g["z"]
+
+
+def test_full_size_sampled(fwbf):
+    """EG(1023,781) at 4 dB with 2^18 frames in one launch; 512 sampled frames
+    checked against the oracle, and every converged frame checks H z = 0."""
+    h = make_code("eg1023")
+    enc = Encoder(h)
+    from paper_1206_3362_gb300.inputs.channel import bpsk_awgn_torch, random_codewords_torch
+
+    F = 1 << 18
+    _, c = random_codewords_torch(enc, F, seed=5, device="cuda")
+    y = bpsk_awgn_torch(c, 4.0, enc.rate, seed=5)
+    with fwbf.Code.from_parity_check(h, 31) as code:
+        q = fwbf.quantize(y)
+        bits, iters = code.decode(q, 100, 1.5)
+        torch.cuda.synchronize()
+    idx = np.random.default_rng(1).choice(F, 512, replace=False)
+    qs = q[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(qs, oracle.quantize(y[torch.from_numpy(idx).cuda()].cpu().numpy()))
+    bo, io, _ = oracle.fwbf_i8_threaded(h, 31, qs, 100, 1.5)
+    assert np.array_equal(iters.cpu().numpy()[idx], io)
+    assert np.array_equal(bits.cpu().numpy().view(np.uint32)[idx], bo)
+    # every converged frame is a codeword (syndrome computed with torch on the device)
+    zb = bits.view(torch.uint8)  # little-endian: byte k holds bits 8k..8k+7
+    z = ((zb.unsqueeze(-1) >> torch.arange(8, device="cuda", dtype=torch.uint8)) & 1).reshape(F, -1)[:, :h.N]
+    Hd = torch.zeros((h.M, h.N), dtype=torch.float32, device="cuda")
+    Hd[torch.from_numpy(h.rows.astype(np.int64)).cuda(), torch.from_numpy(h.cols.astype(np.int64)).cuda()] = 1
+    syn = (z[:65536].float() @ Hd.T).to(torch.int64) % 2
+    conv = iters[:65536] >= 0
+    assert not syn[conv].any() and syn[~conv].any(dim=1).all()
+
+
+# ---------------------------------------------------------------------------
+# float32 decoder against the float64 oracle
+# ---------------------------------------------------------------------------
+
+def _term_scale(h, y, alpha):
+    """sum_m w_{n,m} + alpha |y_n| per bit: the size of the terms of Eq. 1."""
+    a = np.abs(y.astype(np.float64))
+    csr = h.csr()
+    scale = np.zeros_like(a)
+    for m in range(h.M):
+        bits = csr.indices[csr.indptr[m]:csr.indptr[m + 1]]
+        v = a[:, bits]
+        order = np.sort(v, axis=1)
+        m1, m2 = order[:, :1], order[:, 1:2]
+        w = np.where(v == m1, m2, m1)
+        scale[:, bits] += w
+    return scale + alpha * a
+
+
+@pytest.mark.parametrize("key,p", [("eg1023", 31), ("rand504", 32)])
+def test_f32_first_metric(fwbf, key, p):
+    h, c, y = frames(key, 64, 3.5, seed=21)
+    with fwbf.Code.from_parity_check(h, p) as code:
+        E = code.metric_f32(torch.from_numpy(y).cuda(), 1.5).cpu().numpy()
+    _, _, _, e0 = oracle.fwbf_f64(h, p, y, 1, alpha=1.5, want_E0=True)
+    tol = 1e-5 * _term_scale(h, y, 1.5)
+    assert np.all(np.abs(E - e0) <= tol)
+
+
+@pytest.mark.parametrize("key,p,ebn0", [("eg1023", 31, 3.5), ("eg1023", 93, 4.0), ("rand504", 32, 3.0)])
+def test_f32_decisions(fwbf, key, p, ebn0):
+    h, c, y = frames(key, 256, ebn0, seed=22)
+    with fwbf.Code.from_parity_check(h, p) as code:
+        bits, iters = code.decode_f32(torch.from_numpy(y).cuda(), 100, 1.5)
+        bits = bits.cpu().numpy().view(np.uint32)
+        iters = iters.cpu().numpy()
+    bo, io, margin = oracle.fwbf_f64(h, p, y, 100, alpha=1.5)
+    tol = 1e-5 * _term_scale(h, y, 1.5).max(axis=1)
+    clear = margin > 2 * tol
+    same = (iters == io) & (bits == bo).all(axis=1)
+    assert same[clear].all()
+    assert clear.mean() > 0.9, f"near-tie frames: {(~clear).sum()}"
