@@ -106,6 +106,30 @@ int fwbf_decode(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter
                 float alpha, uint32_t *out_bits, int32_t *out_iters, void *stream);
 
 /*
+ * fwbf_decode without any device memory allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory once they are running, such as real-time receivers that fix their
+ * memory at start-up so the decode path has no allocation latency or
+ * out-of-memory failure, and hosts where the stream-ordered allocator is not
+ * available.  fwbf_decode takes its 8-byte frame work counter from a
+ * stream-ordered allocation on every call; this variant takes it from a fixed
+ * 256-byte array in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.  Arguments, results and errors are
+ * those of fwbf_decode.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - The array is shared by every call and keeps the last call's contents; the
+ *     counter is cleared on the stream before each launch.  Calls whose work
+ *     overlaps on the GPU (other streams, other threads) race on it: order them
+ *     on one stream or serialise them.
+ *   - A decode whose scratch would not fit the fixed array is rejected with
+ *     FWBF_EUNSUPPORTED (this decoder needs 8 of the 256 bytes).
+ * No cudaMalloc, cudaFree or other allocating call is made.
+ */
+int fwbf_decode_noalloc(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter,
+                        float alpha, uint32_t *out_bits, int32_t *out_iters, void *stream);
+
+/*
  * FWBF on real channel values, metric of Eq. 1 in float32.
  *   y          device float [n_frames][N] (finite values), any 4-byte alignment
  *   other arguments as fwbf_decode.

@@ -26,6 +26,9 @@
 //   * a pass that flips nothing leaves the state unchanged, so every later pass
 //     repeats it: the frame ends as "not converged" (-max_iter) at once with the
 //     same z.
+#include <mutex>
+#include <string>
+
 #include "device_common.cuh"
 #include "fwbf_internal.h"
 
@@ -350,6 +353,118 @@ int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, in
     cudaError_t e2 = cudaFreeAsync(counter, s);
     if (e != cudaSuccess) return cuda_fail(e, "decode_i8 launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(frame counter)");
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Decoding without any device allocation (fwbf_decode_noalloc).
+//
+// The decoder's only scratch is its frame work counter (8 bytes).  For callers
+// that must not allocate device memory once they are running, the counter is
+// taken from a fixed array that every GPU loading this library holds until the
+// process exits.  All such calls share the array: it is cleared on the stream
+// before each launch, and calls that overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+
+constexpr size_t kNoAllocScratchBytes = 256;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[kMaxDevices];
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device.  (In host code the array's name is only a host-side stand-in.)
+static int noalloc_scratch(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(FWBF_EUNSUPPORTED, "device index above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return 0;
+}
+
+int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                             int theta_q, uint32_t *out_bits, int32_t *out_iters, cudaStream_t s) {
+    const size_t need = sizeof(unsigned long long);
+    if (need > kNoAllocScratchBytes)
+        return fail(FWBF_EUNSUPPORTED, "no-allocation decode needs " + std::to_string(need) +
+                                           " bytes of scratch, above its fixed " +
+                                           std::to_string(kNoAllocScratchBytes) + "-byte array");
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+
+    I8Params P{};
+    P.table = c->d_table;
+    P.table_words = c->table_words;
+    P.N = c->N;
+    P.M = c->M;
+    P.Z = c->Z;
+    P.MB = c->MB;
+    P.NB = c->NB;
+    P.rptr_off = c->rptr_off;
+    P.rent_off = c->rent_off;
+    P.cptr_off = c->cptr_off;
+    P.cent_off = c->cent_off;
+    P.p = c->p;
+    P.B = c->B;
+    P.p_magic = c->p_magic;
+    P.z_magic = c->z_magic;
+    P.y = y;
+    P.F = n_frames;
+    P.max_iter = max_iter;
+    P.alpha_q = alpha_q;
+    P.theta_q = theta_q;
+    P.out_bits = out_bits;
+    P.out_iters = out_iters;
+    const uint32_t N = c->N, M = c->M;
+    uint32_t o = align16(N + 32);
+    P.off_T = o;
+    o += align16(4 * N);
+    P.off_crec = o;
+    o += align16(4 * M);
+    P.off_s = o;
+    o += align16(4 * ((M + 31) / 32));
+    P.off_z = o;
+    o += align16(4 * ((N + 31) / 32));
+    P.off_keys = o;
+    o += align16(8 * (uint32_t)c->B);
+    P.warp_bytes = o;
+    const uint32_t tbytes = c->table_words * 4u;
+    const uint32_t optin = (uint32_t)c->smem_optin;
+    P.table_in_smem = (tbytes + P.warp_bytes + 256u <= optin && tbytes <= 96u * 1024u) ? 1 : 0;
+    P.table_smem_bytes = P.table_in_smem ? tbytes : 0;
+    const uint32_t avail = optin - 256u - P.table_smem_bytes;
+    if (P.warp_bytes > avail) return fail(FWBF_EUNSUPPORTED, "code too large for one warp's shared memory");
+    int warps = (int)(avail / P.warp_bytes);
+    if (warps > 24) warps = 24;
+    const uint32_t dyn = P.table_smem_bytes + warps * P.warp_bytes;
+    auto kern = c->Z == 1 ? fwbf_decode_i8_kernel<true> : fwbf_decode_i8_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(FWBF_EUNSUPPORTED, "decode kernel does not fit on an SM");
+    int64_t blocks = (int64_t)per_sm * c->num_sms;
+    const int64_t blocks_needed = (n_frames + warps - 1) / warps;
+    if (blocks > blocks_needed) blocks = blocks_needed;
+
+    // the counter must start at zero; the array keeps the previous call's value
+    e = cudaMemsetAsync(scratch, 0, need, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-allocation scratch)");
+    P.counter = static_cast<unsigned long long *>(scratch);
+    kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "decode_i8 (no-allocation) launch");
     return 0;
 }
 

@@ -46,6 +46,9 @@ int launch_quantize(const float *y, int8_t *q, int64_t count, cudaStream_t s);
 int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
                      int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
                      cudaStream_t s);
+int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
+                             int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
+                             cudaStream_t s);
 int launch_decode_f32(const fwbf_code_s *c, const float *y, int64_t n_frames, int max_iter,
                       float alpha, float theta, uint32_t *out_bits, int32_t *out_iters,
                       float *out_E, cudaStream_t s);

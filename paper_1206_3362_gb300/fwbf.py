@@ -55,6 +55,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_code_query": ([P, ctypes.POINTER(CodeInfo)], ctypes.c_int),
         "fwbf_quantize": ([P, P, i64, P], ctypes.c_int),
         "fwbf_decode": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
+        "fwbf_decode_noalloc": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_decode_f32": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
         "fwbf_last_status": ([P], ctypes.c_int),
@@ -146,6 +147,19 @@ def fwbf_decode(code, y, max_iter: int, alpha: float, out_bits, out_iters, strea
     _check(load_library().fwbf_decode(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
                                       _dev(out_bits, torch.int32, "out_bits"),
                                       _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
+
+
+def fwbf_decode_noalloc(code, y, max_iter: int, alpha: float, out_bits, out_iters, stream=None) -> None:
+    """fwbf_decode for callers that cannot allocate device memory: the frame
+    counter lives in a fixed array of the library (see include/fwbf.h); calls
+    overlapping on the GPU must not share it."""
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y, info.N)
+    _check(load_library().fwbf_decode_noalloc(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
+                                              _dev(out_bits, torch.int32, "out_bits"),
+                                              _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
 
 
 def fwbf_decode_f32(code, y, max_iter: int, alpha: float, out_bits, out_iters, stream=None) -> None:
