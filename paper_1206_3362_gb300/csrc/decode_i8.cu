@@ -278,8 +278,11 @@ int read_and_clear_status_i8(cudaStream_t s, int *out) {
 
 static inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
-                     int theta_q, uint32_t *out_bits, int32_t *out_iters, cudaStream_t s) {
+// Generic (any H) int8 decoder launch with a caller-provided frame counter
+// that is already zero on the stream.
+static int launch_generic_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                             int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
+                             cudaStream_t s) {
     I8Params P{};
     P.table = c->d_table;
     P.table_words = c->table_words;
@@ -303,6 +306,7 @@ int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, in
     P.theta_q = theta_q;
     P.out_bits = out_bits;
     P.out_iters = out_iters;
+    P.counter = counter;
 
     const uint32_t N = c->N, M = c->M;
     uint32_t o = align16(N + 32);
@@ -338,21 +342,36 @@ int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, in
     int64_t blocks = (int64_t)per_sm * c->num_sms;
     const int64_t need = (n_frames + warps - 1) / warps;
     if (blocks > need) blocks = need;
+    kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "decode_i8 launch");
+    return 0;
+}
 
+// Picks the decoder for the code: the packed cyclic kernel when H is a single
+// circulant it handles, the generic kernel otherwise.
+static int launch_i8_with_counter(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
+                                  int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
+                                  unsigned long long *counter, cudaStream_t s) {
+    if (cyclic_eligible(c))
+        return launch_decode_i8_cyclic(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
+    return launch_generic_i8(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
+}
+
+int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                     int theta_q, uint32_t *out_bits, int32_t *out_iters, cudaStream_t s) {
     unsigned long long *counter = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) {
         cudaFreeAsync(counter, s);
         return cuda_fail(e, "cudaMemsetAsync");
     }
-    P.counter = counter;
-    kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
-    e = cudaGetLastError();
-    cudaError_t e2 = cudaFreeAsync(counter, s);
-    if (e != cudaSuccess) return cuda_fail(e, "decode_i8 launch");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(frame counter)");
+    const int rc = launch_i8_with_counter(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
+    e = cudaFreeAsync(counter, s);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(frame counter)");
     return 0;
 }
 
@@ -402,70 +421,11 @@ int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_fr
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
 
-    I8Params P{};
-    P.table = c->d_table;
-    P.table_words = c->table_words;
-    P.N = c->N;
-    P.M = c->M;
-    P.Z = c->Z;
-    P.MB = c->MB;
-    P.NB = c->NB;
-    P.rptr_off = c->rptr_off;
-    P.rent_off = c->rent_off;
-    P.cptr_off = c->cptr_off;
-    P.cent_off = c->cent_off;
-    P.p = c->p;
-    P.B = c->B;
-    P.p_magic = c->p_magic;
-    P.z_magic = c->z_magic;
-    P.y = y;
-    P.F = n_frames;
-    P.max_iter = max_iter;
-    P.alpha_q = alpha_q;
-    P.theta_q = theta_q;
-    P.out_bits = out_bits;
-    P.out_iters = out_iters;
-    const uint32_t N = c->N, M = c->M;
-    uint32_t o = align16(N + 32);
-    P.off_T = o;
-    o += align16(4 * N);
-    P.off_crec = o;
-    o += align16(4 * M);
-    P.off_s = o;
-    o += align16(4 * ((M + 31) / 32));
-    P.off_z = o;
-    o += align16(4 * ((N + 31) / 32));
-    P.off_keys = o;
-    o += align16(8 * (uint32_t)c->B);
-    P.warp_bytes = o;
-    const uint32_t tbytes = c->table_words * 4u;
-    const uint32_t optin = (uint32_t)c->smem_optin;
-    P.table_in_smem = (tbytes + P.warp_bytes + 256u <= optin && tbytes <= 96u * 1024u) ? 1 : 0;
-    P.table_smem_bytes = P.table_in_smem ? tbytes : 0;
-    const uint32_t avail = optin - 256u - P.table_smem_bytes;
-    if (P.warp_bytes > avail) return fail(FWBF_EUNSUPPORTED, "code too large for one warp's shared memory");
-    int warps = (int)(avail / P.warp_bytes);
-    if (warps > 24) warps = 24;
-    const uint32_t dyn = P.table_smem_bytes + warps * P.warp_bytes;
-    auto kern = c->Z == 1 ? fwbf_decode_i8_kernel<true> : fwbf_decode_i8_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, dyn);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm < 1) return fail(FWBF_EUNSUPPORTED, "decode kernel does not fit on an SM");
-    int64_t blocks = (int64_t)per_sm * c->num_sms;
-    const int64_t blocks_needed = (n_frames + warps - 1) / warps;
-    if (blocks > blocks_needed) blocks = blocks_needed;
-
     // the counter must start at zero; the array keeps the previous call's value
-    e = cudaMemsetAsync(scratch, 0, need, s);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, need, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-allocation scratch)");
-    P.counter = static_cast<unsigned long long *>(scratch);
-    kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "decode_i8 (no-allocation) launch");
-    return 0;
+    return launch_i8_with_counter(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters,
+                                  static_cast<unsigned long long *>(scratch), s);
 }
 
 }  // namespace fwbf

@@ -1,0 +1,485 @@
+// FWBF decoding of int8 channel values for cyclic codes (H a single Z x Z
+// circulant: N = M = Z, N(m) = {(m + d_e) mod Z}, M(n) = {(n + u_e) mod Z},
+// u_e = -d_e mod Z), e.g. the type-I EG(2, 2^s) codes of the paper's Sec. V.
+//
+// Same persistent warp-per-frame model as the generic int8 decoder; what
+// changes is the data layout, which turns every edge loop into aligned,
+// conflict-free shared-memory loads and packed 2 x 16-bit integer arithmetic:
+//
+//   * positions are paired as (i, i + H), H = ceil(Z / 2), i in [0, H).  A
+//     rotation by r maps the pair (i, i + H) onto the positions
+//     (i + r, i + H + r) mod Z, which form again a pair of the "doubled" array
+//     X2[j] = x[j mod Z] | x[(j + H) mod Z] << 16 (j < Z + H).  So for pair i
+//     and offset r the two values are the single word X2[i + r].
+//   * check pass (once per frame): per check pair and row offset, the packed
+//     key |q| << 8 | sign << 7 | e is min/max-reduced with min.u16x2/max.u16x2
+//     into (min1, pos) and min2, and the sign bits XOR into the parity.
+//   * w_{n,m} = min1_m except w = min2_m at the row position pos_m holding
+//     min1 (the minimum over N(m)\n).  Hence
+//       tot_n = sum_{m in M(n)} w_{n,m} = sum_{m in M(n)} min1_m + corrections,
+//       U_n   = sum_{m in M(n), s_m = 1} w_{n,m}
+//             = sum_{m in M(n)} s_m min1_m + corrections,
+//     where each check adds (min2_m - min1_m) [times s_m] to its one arg-min
+//     bit.  The sums over M(n) are gathers over the doubled array of
+//     V_m = min1_m (once) or s_m min1_m (every pass): one load and one packed
+//     add per two edges; the corrections are one shared atomic per check.
+//   * E'_n = 256 (2 U_n - tot_n) - alpha_q a_n, block arg-max, flips, syndrome
+//     toggles and the no-flip shortcut are those of the generic decoder.
+// All integer results equal the definition (Sec. III, Eq. 1) exactly.
+#include "device_common.cuh"
+#include "fwbf_internal.h"
+
+namespace fwbf {
+
+__device__ int g_status_i8_cyclic;
+
+struct CyclicParams {
+    const uint32_t *table;
+    uint32_t table_words, table_smem_bytes;
+    uint32_t rent_off, cent_off;
+    int Z, H, DC;
+    int p, B;
+    uint32_t p_magic;
+    const int8_t *y;
+    int64_t F;
+    int max_iter, alpha_q, theta_q;
+    uint32_t *out_bits;
+    int32_t *out_iters;
+    unsigned long long *counter;
+    int dense_above;  // passes with more unsatisfied checks use the dense gather
+    uint32_t warp_bytes, off_X, off_crec, off_BT, off_UP, off_V, off_s, off_z, off_keys;
+};
+
+__device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t vmax_u16x2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// packed check key of one int8 value: |q| << 8 | (q < 0) << 7
+__device__ __forceinline__ uint32_t qkey(int v) { return ((uint32_t)abs(v) << 8) | ((v < 0) ? 0x80u : 0u); }
+
+// dst[i] (+)= sum_e X2[i + u_e] for the lane's pairs i = lane + 32 (R c + r):
+// the packed gather over M(n) of both positions of every pair.
+template <int R, bool ACCUMULATE>
+__device__ __forceinline__ void gather_pairs(const uint32_t *__restrict__ X2, const uint32_t *__restrict__ u_off, int DC,
+                                          uint32_t *__restrict__ dst, int lane, int chunks) {
+    for (int c = 0; c < chunks; ++c) {
+        uint32_t acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0u;
+        const uint32_t *xb = X2 + lane + 32 * R * c;
+        int e = 0;
+        for (; e + 1 < DC; e += 2) {
+            const uint32_t *p0 = xb + u_off[e];
+            const uint32_t *p1 = xb + u_off[e + 1];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += p0[32 * r] + p1[32 * r];
+        }
+        if (e < DC) {
+            const uint32_t *p0 = xb + u_off[e];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] += p0[32 * r];
+        }
+        uint32_t *db = dst + lane + 32 * R * c;
+#pragma unroll
+        for (int r = 0; r < R; ++r) db[32 * r] = ACCUMULATE ? db[32 * r] + acc[r] : acc[r];
+    }
+}
+
+// pair slot of position n: (n, lo) for n < H, (n - H, hi) otherwise
+__device__ __forceinline__ void pair_slot(int n, int H, int &idx, int &shift) {
+    const bool hi = n >= H;
+    idx = hi ? n - H : n;
+    shift = hi ? 16 : 0;
+}
+
+template <int R>  // pairs per lane per chunk
+__global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const CyclicParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ int flag;
+    __shared__ uint32_t d_off[128], u_off[128];
+
+    {
+        uint32_t *st = reinterpret_cast<uint32_t *>(smem);
+        if (!stage_table(st, P.table, P.table_words, &bar, &flag)) {
+            if (threadIdx.x == 0) atomicOr(&g_status_i8_cyclic, 1);
+            return;
+        }
+        for (int e = threadIdx.x; e < P.DC; e += blockDim.x) {
+            d_off[e] = st[P.rent_off + e] & 0xffffu;
+            u_off[e] = st[P.cent_off + e] & 0xffffu;
+        }
+        __syncthreads();
+    }
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char *ws = smem + P.table_smem_bytes + warp * P.warp_bytes;
+    int8_t *stage = reinterpret_cast<int8_t *>(ws);
+    uint32_t *X2 = reinterpret_cast<uint32_t *>(ws + P.off_X);
+    uint32_t *crec = reinterpret_cast<uint32_t *>(ws + P.off_crec);
+    uint32_t *BT = reinterpret_cast<uint32_t *>(ws + P.off_BT);
+    uint32_t *UP = reinterpret_cast<uint32_t *>(ws + P.off_UP);
+    uint32_t *Vw = reinterpret_cast<uint32_t *>(ws + P.off_V);  // V_m = s_m min1_m, two u16 per word
+    const uint16_t *V = reinterpret_cast<const uint16_t *>(Vw);
+    uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
+    uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
+
+    const int Z = P.Z, H = P.H, DC = P.DC;
+    const int Zw = (Z + 31) >> 5;
+    const int XJ = Z + H - 1;  // doubled-array words used: i + r <= H - 1 + Z - 1
+    const int chunks = H / (32 * R);
+    const uintptr_t ybase = reinterpret_cast<uintptr_t>(P.y);
+    const uintptr_t yend = ybase + (uintptr_t)(P.F * (int64_t)Z);
+
+    for (int b = lane; b < P.B; b += 32) keys[b] = 0ull;
+
+    for (;;) {
+        unsigned long long f = 0;
+        if (lane == 0) f = atomicAdd(P.counter, 1ull);
+        f = __shfl_sync(FULL, f, 0);
+        if (f >= (unsigned long long)P.F) break;
+
+        // ---- frame load (aligned 16-byte chunks; byte loads at the buffer end)
+        const uintptr_t fb = ybase + (uintptr_t)(f * (unsigned long long)Z);
+        const uintptr_t a0 = fb & ~(uintptr_t)15;
+        const int off = (int)(fb - a0);
+        const int nchunks = (off + Z + 15) >> 4;
+        for (int c = lane; c < nchunks; c += 32) {
+            const uintptr_t src = a0 + (uintptr_t)c * 16;
+            uint4 v;
+            if (src + 16 <= yend) {
+                v = __ldcs(reinterpret_cast<const uint4 *>(src));
+            } else {
+                uint32_t wv[4] = {0u, 0u, 0u, 0u};
+                for (int i = 0; i < 16; ++i)
+                    if (src + i < yend)
+                        wv[i >> 2] |= (uint32_t)(*reinterpret_cast<const unsigned char *>(src + i)) << (8 * (i & 3));
+                v = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+            *reinterpret_cast<uint4 *>(stage + c * 16) = v;
+        }
+        for (int i = lane; i < H; i += 32) UP[i] = 0u;
+        __syncwarp();
+        const int8_t *q = stage + off;
+
+        for (int w = 0; w < Zw; ++w) {
+            const int n = (w << 5) + lane;
+            const uint32_t zb = __ballot_sync(FULL, n < Z && q[n] < 0);
+            if (lane == 0) zbits[w] = zb;
+        }
+        // doubled array of check keys
+        for (int j = lane; j < XJ; j += 32) {
+            const int n0 = j < Z ? j : j - Z;
+            int n1 = j + H;
+            n1 = n1 >= Z ? n1 - Z : n1;
+            X2[j] = qkey(q[n0]) | (qkey(q[n1]) << 16);
+        }
+        __syncwarp();
+
+        // ---- check pass: min1/pos, min2 and parity of every check pair -------
+        int W = 0;
+        for (int c = 0; c < chunks; ++c) {
+            uint32_t k1[R], k2[R], par[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                k1[r] = 0xffffffffu;
+                k2[r] = 0xffffffffu;
+                par[r] = 0u;
+            }
+            const uint32_t *xb = X2 + lane + 32 * R * c;
+            for (int e = 0; e < DC; ++e) {
+                const uint32_t *p = xb + d_off[e];
+                const uint32_t ek = (uint32_t)e | ((uint32_t)e << 16);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t v = p[32 * r];
+                    const uint32_t key = v | ek;
+                    k2[r] = vmin_u16x2(k2[r], vmax_u16x2(k1[r], key));
+                    k1[r] = vmin_u16x2(k1[r], key);
+                    par[r] ^= v;
+                }
+            }
+            for (int r = 0; r < R; ++r) {
+                const int i = lane + 32 * (R * c + r);
+                const uint32_t min1_lo = (k1[r] >> 8) & 0x7fu, min1_hi = (k1[r] >> 24) & 0x7fu;
+                const uint32_t s_lo = (par[r] >> 7) & 1u;
+                const bool hi_ok = i + H < Z;
+                const uint32_t s_hi = hi_ok ? (par[r] >> 23) & 1u : 0u;
+                crec[i] = min1_lo | (((k2[r] >> 8) & 0x7fu) << 8) | ((k1[r] & 0x7fu) << 16);
+                if (hi_ok) crec[i + H] = min1_hi | (((k2[r] >> 24) & 0x7fu) << 8) | (((k1[r] >> 16) & 0x7fu) << 16);
+                const uint32_t slo = __ballot_sync(FULL, s_lo);
+                const uint32_t shi = __ballot_sync(FULL, s_hi);
+                if (lane == 0) {
+                    sbits[R * c + r] = slo;
+                    sbits[(H >> 5) + R * c + r] = shi;
+                }
+                W += __popc(slo) + __popc(shi);
+            }
+        }
+        __syncwarp();
+
+        // V_m = s_m min1_m (plain layout) and the doubled array of min1
+        for (int m2 = lane; 2 * m2 < Z; m2 += 32) {
+            const int m = 2 * m2;
+            const uint32_t sw = sbits[m >> 5] >> (m & 31);
+            const uint32_t v0 = (sw & 1u) ? (crec[m] & 0x7fu) : 0u;
+            const uint32_t v1 = (m + 1 < Z && ((sw >> 1) & 1u)) ? (crec[m + 1] & 0x7fu) : 0u;
+            Vw[m2] = v0 | (v1 << 16);
+        }
+        for (int j = lane; j < XJ; j += 32) {
+            const int n0 = j < Z ? j : j - Z;
+            int n1 = j + H;
+            n1 = n1 >= Z ? n1 - Z : n1;
+            X2[j] = (crec[n0] & 0x7fu) | ((crec[n1] & 0x7fu) << 16);
+        }
+        __syncwarp();
+
+        // ---- tot_n: gather of min1 over M(n), then the arg-min corrections ----
+        gather_pairs<R, false>(X2, u_off, DC, BT, lane, chunks);
+        __syncwarp();
+        for (int m = lane; m < Z; m += 32) {
+            const uint32_t rec = crec[m];
+            const uint32_t diff = ((rec >> 8) & 0x7fu) - (rec & 0x7fu);
+            if (diff) {
+                int n = m + (int)d_off[rec >> 16];
+                n = n >= Z ? n - Z : n;
+                int idx, sh;
+                pair_slot(n, H, idx, sh);
+                atomicAdd(&BT[idx], diff << sh);
+            }
+        }
+        __syncwarp();
+
+        // ---- iterations ------------------------------------------------------
+        int iters;
+        for (int k = 0;; ++k) {
+            if (W == 0) {
+                iters = k;
+                break;
+            }
+            if (k == P.max_iter) {
+                iters = -P.max_iter;
+                break;
+            }
+            if (W > P.dense_above) {
+                // dense: doubled array of V, arg-min corrections, packed gather
+                for (int j = lane; j < XJ; j += 32) {
+                    const int n0 = j < Z ? j : j - Z;
+                    int n1 = j + H;
+                    n1 = n1 >= Z ? n1 - Z : n1;
+                    X2[j] = (uint32_t)V[n0] | ((uint32_t)V[n1] << 16);
+                }
+                for (int wd = lane; wd < Zw; wd += 32) {
+                    uint32_t bits = sbits[wd];
+                    while (bits) {
+                        const int j = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const int m = (wd << 5) + j;
+                        const uint32_t rec = crec[m];
+                        const uint32_t diff = ((rec >> 8) & 0x7fu) - (rec & 0x7fu);
+                        if (diff) {
+                            int n = m + (int)d_off[rec >> 16];
+                            n = n >= Z ? n - Z : n;
+                            int idx, sh;
+                            pair_slot(n, H, idx, sh);
+                            atomicAdd(&UP[idx], diff << sh);
+                        }
+                    }
+                }
+                __syncwarp();
+                gather_pairs<R, true>(X2, u_off, DC, UP, lane, chunks);
+            } else {
+                // sparse: the warp scatters w of every unsatisfied check, one
+                // row position per lane
+                for (int wd = 0; wd < Zw; ++wd) {
+                    uint32_t bits = sbits[wd];
+                    while (bits) {
+                        const int j = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const int m = (wd << 5) + j;
+                        const uint32_t rec = crec[m];
+                        const uint32_t min1 = rec & 0x7fu, min2 = (rec >> 8) & 0x7fu, pos = rec >> 16;
+                        for (int e = lane; e < DC; e += 32) {
+                            int n = m + (int)d_off[e];
+                            n = n >= Z ? n - Z : n;
+                            int idx, sh;
+                            pair_slot(n, H, idx, sh);
+                            atomicAdd(&UP[idx], ((uint32_t)e == pos ? min2 : min1) << sh);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            // metric and per-block candidates
+            for (int i = lane; i < H; i += 32) {
+                const uint32_t U2 = UP[i];
+                if (U2 == 0u) continue;  // U = 0 gives E' <= 0: never a candidate
+                UP[i] = 0u;
+                const uint32_t T2 = BT[i];
+                for (int half = 0; half < 2; ++half) {
+                    const int n = i + half * H;
+                    const int U = (int)((U2 >> (16 * half)) & 0xffffu);
+                    if (U == 0 || n >= Z) continue;
+                    const int tot = (int)((T2 >> (16 * half)) & 0xffffu);
+                    const int E = (2 * U - tot) * 256 - P.alpha_q * abs((int)q[n]);
+                    if (E > P.theta_q) {
+                        const uint32_t blk = div_small((uint32_t)n, P.p, P.p_magic);
+                        const unsigned long long key =
+                            ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - (uint32_t)n);
+                        atomicMax(&keys[blk], key);
+                    }
+                }
+            }
+            __syncwarp();
+            // flips: the warp toggles the checks of one flipped bit at a time
+            int dW = 0, nflip = 0;
+            for (int b0 = 0; b0 < P.B; b0 += 32) {
+                const int b = b0 + lane;
+                unsigned long long key = 0ull;
+                if (b < P.B) {
+                    key = keys[b];
+                    if (key) keys[b] = 0ull;
+                }
+                uint32_t pend = __ballot_sync(FULL, key != 0ull);
+                nflip += __popc(pend);
+                while (pend) {
+                    const int src = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    const uint32_t n = 0xffffffffu - (uint32_t)__shfl_sync(FULL, key, src);
+                    if (lane == 0) zbits[n >> 5] ^= 1u << (n & 31);
+                    for (int e = lane; e < DC; e += 32) {
+                        uint32_t m = n + u_off[e];
+                        m = m >= (uint32_t)Z ? m - Z : m;
+                        const uint32_t bit = 1u << (m & 31);
+                        const uint32_t old = atomicXor(&sbits[m >> 5], bit);
+                        dW += (old & bit) ? -1 : 1;
+                        atomicXor(&Vw[m >> 1], (crec[m] & 0x7fu) << (16 * (m & 1)));
+                    }
+                }
+            }
+            W += warp_sum(dW);
+            __syncwarp();
+            if (nflip == 0) {
+                iters = -P.max_iter;
+                break;
+            }
+        }
+
+        uint32_t *ob = P.out_bits + f * (unsigned long long)Zw;
+        for (int w = lane; w < Zw; w += 32) __stcs(ob + w, zbits[w]);
+        if (lane == 0) P.out_iters[f] = iters;
+        __syncwarp();
+    }
+}
+
+static inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+bool cyclic_eligible(const fwbf_code_s *c) {
+    if (c->Z != c->N || c->N != c->M || c->MB != 1 || c->NB != 1) return false;
+    const int H = (c->Z + 1) / 2;
+    if (H % 32 != 0) return false;
+    if (c->dc_max > 127 || c->dc_max != c->dv_max) return false;
+    return true;
+}
+
+int read_and_clear_status_i8_cyclic(cudaStream_t s, int *out) {
+    int v = 0, zero = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    e = cudaMemcpyFromSymbol(&v, g_status_i8_cyclic, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyFromSymbol(status)");
+    if (v) {
+        e = cudaMemcpyToSymbol(g_status_i8_cyclic, &zero, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyToSymbol(status)");
+    }
+    *out = v;
+    return 0;
+}
+
+int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                            int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
+                            cudaStream_t s) {
+    CyclicParams P{};
+    P.table = c->d_table;
+    P.table_words = c->table_words;
+    P.rent_off = c->rent_off;
+    P.cent_off = c->cent_off;
+    P.Z = c->Z;
+    P.H = (c->Z + 1) / 2;
+    P.DC = c->dc_max;
+    P.p = c->p;
+    P.B = c->B;
+    P.p_magic = c->p_magic;
+    P.y = y;
+    P.F = n_frames;
+    P.max_iter = max_iter;
+    P.alpha_q = alpha_q;
+    P.theta_q = theta_q;
+    P.out_bits = out_bits;
+    P.out_iters = out_iters;
+    P.counter = counter;
+    P.dense_above = 128;
+
+    const uint32_t Z = c->Z, H = P.H;
+    uint32_t o = align16(Z + 32);
+    P.off_X = o;
+    o += align16(4 * (Z + H));
+    P.off_crec = o;
+    o += align16(4 * Z);
+    P.off_BT = o;
+    o += align16(4 * H);
+    P.off_UP = o;
+    o += align16(4 * H);
+    P.off_V = o;
+    o += align16(2 * (Z + 1));
+    P.off_s = o;
+    o += align16(4 * ((Z + 31) / 32));
+    P.off_z = o;
+    o += align16(4 * ((Z + 31) / 32));
+    P.off_keys = o;
+    o += align16(8 * (uint32_t)c->B);
+    P.warp_bytes = o;
+    P.table_smem_bytes = align16(c->table_words * 4u);
+    const uint32_t optin = (uint32_t)c->smem_optin;
+    const uint32_t reserve = 2048u;  // static shared memory of the kernel
+    if (P.table_smem_bytes + P.warp_bytes + reserve > optin)
+        return fail(FWBF_EUNSUPPORTED, "cyclic code too large for one warp's shared memory");
+    int warps = (int)((optin - reserve - P.table_smem_bytes) / P.warp_bytes);
+    if (warps > 16) warps = 16;
+    const uint32_t dyn = P.table_smem_bytes + warps * P.warp_bytes;
+
+    const int pairs_per_lane = (int)H / 32;
+    void (*kern)(const CyclicParams);
+    if (pairs_per_lane % 8 == 0)
+        kern = fwbf_decode_i8_cyclic_kernel<8>;
+    else if (pairs_per_lane % 4 == 0)
+        kern = fwbf_decode_i8_cyclic_kernel<4>;
+    else if (pairs_per_lane % 2 == 0)
+        kern = fwbf_decode_i8_cyclic_kernel<2>;
+    else
+        kern = fwbf_decode_i8_cyclic_kernel<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, dyn);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(FWBF_EUNSUPPORTED, "cyclic decode kernel does not fit on an SM");
+    int64_t blocks = (int64_t)per_sm * c->num_sms;
+    const int64_t need = (n_frames + warps - 1) / warps;
+    if (blocks > need) blocks = need;
+    kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "decode_i8_cyclic launch");
+    return 0;
+}
+
+}  // namespace fwbf

@@ -46,6 +46,11 @@ int launch_quantize(const float *y, int8_t *q, int64_t count, cudaStream_t s);
 int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
                      int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
                      cudaStream_t s);
+bool cyclic_eligible(const fwbf_code_s *c);
+int read_and_clear_status_i8_cyclic(cudaStream_t s, int *out);
+int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                            int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
+                            cudaStream_t s);
 int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
                              int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
                              cudaStream_t s);

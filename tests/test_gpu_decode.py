@@ -109,6 +109,22 @@ def test_other_codes(fwbf, key, p):
     assert_same(fwbf, h, p, oracle.quantize(y), 30, 1.5)
 
 
+def test_generic_kernel_on_permuted_eg1023(fwbf):
+    """The same EG(1023,781) code with its columns permuted has no circulant
+    structure, so it runs through the generic (list-based) kernel instead of
+    the packed cyclic one; both must match the oracle."""
+    from paper_1206_3362_gb300.inputs.codes import ParityCheck
+
+    h0, c, y = frames("eg1023", 256, 3.5, seed=31)
+    perm = np.random.default_rng(0).permutation(h0.N)
+    h = ParityCheck(N=h0.N, M=h0.M, rows=h0.rows, cols=perm[h0.cols].astype(np.int32))
+    yp = np.empty_like(y)
+    yp[:, perm] = y
+    with fwbf.Code.from_parity_check(h, 31) as code:
+        assert code.info.Z == 1
+    assert_same(fwbf, h, 31, oracle.quantize(yp), 100, 1.5)
+
+
 def test_circulant_structure_detected(fwbf):
     for key, Z in (("eg1023", 1023), ("qc8192", 256), ("rand504", 1)):
         h = make_code(key)
