@@ -15,16 +15,17 @@
 //     key |q| << 8 | sign << 7 | e is min/max-reduced with min.u16x2/max.u16x2
 //     into (min1, pos) and min2, and the sign bits XOR into the parity.
 //   * w_{n,m} = min1_m except w = min2_m at the row position pos_m holding
-//     min1 (the minimum over N(m)\n).  Hence
-//       tot_n = sum_{m in M(n)} w_{n,m} = sum_{m in M(n)} min1_m + corrections,
-//       U_n   = sum_{m in M(n), s_m = 1} w_{n,m}
-//             = sum_{m in M(n)} s_m min1_m + corrections,
-//     where each check adds (min2_m - min1_m) [times s_m] to its one arg-min
-//     bit.  The sums over M(n) are gathers over the doubled array of
-//     V_m = min1_m (once) or s_m min1_m (every pass): one load and one packed
-//     add per two edges; the corrections are one shared atomic per check.
-//   * E'_n = 256 (2 U_n - tot_n) - alpha_q a_n, block arg-max, flips, syndrome
-//     toggles and the no-flip shortcut are those of the generic decoder.
+//     min1 (the minimum over N(m)\n).  With diff_m = min2_m - min1_m,
+//       D_n = sum_{m in M(n)} (2 s_m - 1) w_{n,m}
+//           = sum_{m in M(n)} V'_m - 128 d_c + 2 UC_n - TC_n,
+//     V'_m = (2 s_m - 1) min1_m + 128 (in [1, 255], so packed sums never carry),
+//     TC_n = sum of diff_m over the checks whose arg-min bit is n (fixed) and
+//     UC_n = the same sum over those checks with s_m = 1.  The sum over M(n)
+//     is a gather over the doubled array of V': one load and one packed add per
+//     two edges.  Every syndrome toggle updates V' (+-2 min1) and UC (+-diff)
+//     in place, so a pass is one gather plus its metric epilogue.
+//   * E'_n = 256 D_n - alpha_q a_n (Eq. 1 times 256); block arg-max, flips and
+//     the no-flip shortcut are those of the generic decoder.
 // All integer results equal the definition (Sec. III, Eq. 1) exactly.
 #include "device_common.cuh"
 #include "fwbf_internal.h"
@@ -46,8 +47,7 @@ struct CyclicParams {
     uint32_t *out_bits;
     int32_t *out_iters;
     unsigned long long *counter;
-    int dense_above;  // passes with more unsatisfied checks use the dense gather
-    uint32_t warp_bytes, off_X, off_crec, off_BT, off_UP, off_V, off_s, off_z, off_keys;
+    uint32_t warp_bytes, off_X, off_crec, off_TA, off_UC, off_s, off_z, off_keys;
 };
 
 __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
@@ -64,39 +64,34 @@ __device__ __forceinline__ uint32_t vmax_u16x2(uint32_t a, uint32_t b) {
 // packed check key of one int8 value: |q| << 8 | (q < 0) << 7
 __device__ __forceinline__ uint32_t qkey(int v) { return ((uint32_t)abs(v) << 8) | ((v < 0) ? 0x80u : 0u); }
 
-// dst[i] (+)= sum_e X2[i + u_e] for the lane's pairs i = lane + 32 (R c + r):
-// the packed gather over M(n) of both positions of every pair.
-template <int R, bool ACCUMULATE>
-__device__ __forceinline__ void gather_pairs(const uint32_t *__restrict__ X2, const uint32_t *__restrict__ u_off, int DC,
-                                          uint32_t *__restrict__ dst, int lane, int chunks) {
-    for (int c = 0; c < chunks; ++c) {
-        uint32_t acc[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = 0u;
-        const uint32_t *xb = X2 + lane + 32 * R * c;
-        int e = 0;
-        for (; e + 1 < DC; e += 2) {
-            const uint32_t *p0 = xb + u_off[e];
-            const uint32_t *p1 = xb + u_off[e + 1];
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] += p0[32 * r] + p1[32 * r];
-        }
-        if (e < DC) {
-            const uint32_t *p0 = xb + u_off[e];
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] += p0[32 * r];
-        }
-        uint32_t *db = dst + lane + 32 * R * c;
-#pragma unroll
-        for (int r = 0; r < R; ++r) db[32 * r] = ACCUMULATE ? db[32 * r] + acc[r] : acc[r];
-    }
-}
-
 // pair slot of position n: (n, lo) for n < H, (n - H, hi) otherwise
 __device__ __forceinline__ void pair_slot(int n, int H, int &idx, int &shift) {
     const bool hi = n >= H;
     idx = hi ? n - H : n;
     shift = hi ? 16 : 0;
+}
+
+// Rebuilds the doubled array X2[j] = v(j mod Z) | v((j + H) mod Z) << 16.
+template <typename F>
+__device__ __forceinline__ void build_doubled(uint32_t *X2, int Z, int H, int XJ, int lane, F v) {
+    for (int j = lane; j < XJ; j += 32) {
+        const int n0 = j < Z ? j : j - Z;
+        int n1 = j + H;
+        n1 = n1 >= Z ? n1 - Z : n1;
+        X2[j] = v(n0) | (v(n1) << 16);
+    }
+}
+
+// Adds delta to every half-word of the doubled array that holds position m
+// (the half-words stay in [1, 255], so no carry or borrow crosses halves).
+__device__ __forceinline__ void doubled_add(uint32_t *X2, int m, int delta, int Z, int H, int XJ) {
+    const uint32_t lo = (uint32_t)delta, hi = (uint32_t)delta * 65536u;
+    atomicAdd(&X2[m], lo);
+    if (m + Z < XJ) atomicAdd(&X2[m + Z], lo);
+    int jh = m - H;
+    if (jh < 0) jh += Z;
+    atomicAdd(&X2[jh], hi);
+    if (jh + Z < XJ) atomicAdd(&X2[jh + Z], hi);
 }
 
 template <int R>  // pairs per lane per chunk
@@ -125,10 +120,9 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
     int8_t *stage = reinterpret_cast<int8_t *>(ws);
     uint32_t *X2 = reinterpret_cast<uint32_t *>(ws + P.off_X);
     uint32_t *crec = reinterpret_cast<uint32_t *>(ws + P.off_crec);
-    uint32_t *BT = reinterpret_cast<uint32_t *>(ws + P.off_BT);
-    uint32_t *UP = reinterpret_cast<uint32_t *>(ws + P.off_UP);
-    uint32_t *Vw = reinterpret_cast<uint32_t *>(ws + P.off_V);  // V_m = s_m min1_m, two u16 per word
-    const uint16_t *V = reinterpret_cast<const uint16_t *>(Vw);
+    uint2 *TA = reinterpret_cast<uint2 *>(ws + P.off_TA);  // (tot pair, |q| pair) per position pair
+    uint32_t *TAw = reinterpret_cast<uint32_t *>(TA);
+    uint32_t *UC = reinterpret_cast<uint32_t *>(ws + P.off_UC);
     uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
@@ -139,6 +133,8 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
     const int chunks = H / (32 * R);
     const uintptr_t ybase = reinterpret_cast<uintptr_t>(P.y);
     const uintptr_t yend = ybase + (uintptr_t)(P.F * (int64_t)Z);
+    const uint32_t my_u = lane < DC ? u_off[lane] : 0u;  // column offset of row position e = lane
+    const int bias = 128 * DC;
 
     for (int b = lane; b < P.B; b += 32) keys[b] = 0ull;
 
@@ -167,25 +163,24 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
             }
             *reinterpret_cast<uint4 *>(stage + c * 16) = v;
         }
-        for (int i = lane; i < H; i += 32) UP[i] = 0u;
         __syncwarp();
         const int8_t *q = stage + off;
+        for (int i = lane; i < H; i += 32) {
+            const int n1 = i + H < Z ? i + H : i + H - Z;
+            UC[i] = 0u;
+            TA[i] = make_uint2(0u, (uint32_t)abs((int)q[i]) | ((uint32_t)abs((int)q[n1]) << 16));
+        }
 
         for (int w = 0; w < Zw; ++w) {
             const int n = (w << 5) + lane;
             const uint32_t zb = __ballot_sync(FULL, n < Z && q[n] < 0);
             if (lane == 0) zbits[w] = zb;
         }
-        // doubled array of check keys
-        for (int j = lane; j < XJ; j += 32) {
-            const int n0 = j < Z ? j : j - Z;
-            int n1 = j + H;
-            n1 = n1 >= Z ? n1 - Z : n1;
-            X2[j] = qkey(q[n0]) | (qkey(q[n1]) << 16);
-        }
+        build_doubled(X2, Z, H, XJ, lane, [&](int n) { return qkey(q[n]); });
         __syncwarp();
 
-        // ---- check pass: min1/pos, min2 and parity of every check pair -------
+        // ---- check pass: min1/pos, min2 and parity of every check pair; the
+        //      arg-min corrections of tot (into TA.x) and of U (into UC) ------
         int W = 0;
         for (int c = 0; c < chunks; ++c) {
             uint32_t k1[R], k2[R], par[R];
@@ -210,12 +205,26 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
             }
             for (int r = 0; r < R; ++r) {
                 const int i = lane + 32 * (R * c + r);
-                const uint32_t min1_lo = (k1[r] >> 8) & 0x7fu, min1_hi = (k1[r] >> 24) & 0x7fu;
-                const uint32_t s_lo = (par[r] >> 7) & 1u;
                 const bool hi_ok = i + H < Z;
+                const uint32_t s_lo = (par[r] >> 7) & 1u;
                 const uint32_t s_hi = hi_ok ? (par[r] >> 23) & 1u : 0u;
-                crec[i] = min1_lo | (((k2[r] >> 8) & 0x7fu) << 8) | ((k1[r] & 0x7fu) << 16);
-                if (hi_ok) crec[i + H] = min1_hi | (((k2[r] >> 24) & 0x7fu) << 8) | (((k1[r] >> 16) & 0x7fu) << 16);
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    if (half && !hi_ok) break;
+                    const int m = i + half * H;
+                    const uint32_t a1 = k1[r] >> (16 * half), a2 = k2[r] >> (16 * half);
+                    const uint32_t min1 = (a1 >> 8) & 0x7fu, pos = a1 & 0x7fu, min2 = (a2 >> 8) & 0x7fu;
+                    crec[m] = min1 | (min2 << 8) | (pos << 16);
+                    const uint32_t diff = min2 - min1;
+                    if (diff) {
+                        int n = m + (int)d_off[pos];
+                        n = n >= Z ? n - Z : n;
+                        int idx, sh;
+                        pair_slot(n, H, idx, sh);
+                        atomicAdd(&TAw[2 * idx], diff << sh);
+                        if (half ? s_hi : s_lo) atomicAdd(&UC[idx], diff << sh);
+                    }
+                }
                 const uint32_t slo = __ballot_sync(FULL, s_lo);
                 const uint32_t shi = __ballot_sync(FULL, s_hi);
                 if (lane == 0) {
@@ -227,36 +236,11 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
         }
         __syncwarp();
 
-        // V_m = s_m min1_m (plain layout) and the doubled array of min1
-        for (int m2 = lane; 2 * m2 < Z; m2 += 32) {
-            const int m = 2 * m2;
-            const uint32_t sw = sbits[m >> 5] >> (m & 31);
-            const uint32_t v0 = (sw & 1u) ? (crec[m] & 0x7fu) : 0u;
-            const uint32_t v1 = (m + 1 < Z && ((sw >> 1) & 1u)) ? (crec[m + 1] & 0x7fu) : 0u;
-            Vw[m2] = v0 | (v1 << 16);
-        }
-        for (int j = lane; j < XJ; j += 32) {
-            const int n0 = j < Z ? j : j - Z;
-            int n1 = j + H;
-            n1 = n1 >= Z ? n1 - Z : n1;
-            X2[j] = (crec[n0] & 0x7fu) | ((crec[n1] & 0x7fu) << 16);
-        }
-        __syncwarp();
-
-        // ---- tot_n: gather of min1 over M(n), then the arg-min corrections ----
-        gather_pairs<R, false>(X2, u_off, DC, BT, lane, chunks);
-        __syncwarp();
-        for (int m = lane; m < Z; m += 32) {
-            const uint32_t rec = crec[m];
-            const uint32_t diff = ((rec >> 8) & 0x7fu) - (rec & 0x7fu);
-            if (diff) {
-                int n = m + (int)d_off[rec >> 16];
-                n = n >= Z ? n - Z : n;
-                int idx, sh;
-                pair_slot(n, H, idx, sh);
-                atomicAdd(&BT[idx], diff << sh);
-            }
-        }
+        // the doubled array of V'_m = (2 s_m - 1) min1_m + 128, kept current
+        build_doubled(X2, Z, H, XJ, lane, [&](int n) {
+            const uint32_t mn = crec[n] & 0x7fu;
+            return ((sbits[n >> 5] >> (n & 31)) & 1u) ? 128u + mn : 128u - mn;
+        });
         __syncwarp();
 
         // ---- iterations ------------------------------------------------------
@@ -270,77 +254,42 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
                 iters = -P.max_iter;
                 break;
             }
-            if (W > P.dense_above) {
-                // dense: doubled array of V, arg-min corrections, packed gather
-                for (int j = lane; j < XJ; j += 32) {
-                    const int n0 = j < Z ? j : j - Z;
-                    int n1 = j + H;
-                    n1 = n1 >= Z ? n1 - Z : n1;
-                    X2[j] = (uint32_t)V[n0] | ((uint32_t)V[n1] << 16);
+            // D_n = sum (2 s_m - 1) w_{n,m} = G_n - 128 d_c + 2 UC_n - TC_n with
+            // G the gather of V' over M(n); metric E' = 256 D_n - alpha_q a_n
+            for (int c = 0; c < chunks; ++c) {
+                uint32_t acc[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = 0u;
+                const uint32_t *xb = X2 + lane + 32 * R * c;
+                for (int e = 0; e < DC; ++e) {
+                    const uint32_t *p = xb + u_off[e];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += p[32 * r];
                 }
-                for (int wd = lane; wd < Zw; wd += 32) {
-                    uint32_t bits = sbits[wd];
-                    while (bits) {
-                        const int j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const int m = (wd << 5) + j;
-                        const uint32_t rec = crec[m];
-                        const uint32_t diff = ((rec >> 8) & 0x7fu) - (rec & 0x7fu);
-                        if (diff) {
-                            int n = m + (int)d_off[rec >> 16];
-                            n = n >= Z ? n - Z : n;
-                            int idx, sh;
-                            pair_slot(n, H, idx, sh);
-                            atomicAdd(&UP[idx], diff << sh);
-                        }
-                    }
-                }
-                __syncwarp();
-                gather_pairs<R, true>(X2, u_off, DC, UP, lane, chunks);
-            } else {
-                // sparse: the warp scatters w of every unsatisfied check, one
-                // row position per lane
-                for (int wd = 0; wd < Zw; ++wd) {
-                    uint32_t bits = sbits[wd];
-                    while (bits) {
-                        const int j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const int m = (wd << 5) + j;
-                        const uint32_t rec = crec[m];
-                        const uint32_t min1 = rec & 0x7fu, min2 = (rec >> 8) & 0x7fu, pos = rec >> 16;
-                        for (int e = lane; e < DC; e += 32) {
-                            int n = m + (int)d_off[e];
-                            n = n >= Z ? n - Z : n;
-                            int idx, sh;
-                            pair_slot(n, H, idx, sh);
-                            atomicAdd(&UP[idx], ((uint32_t)e == pos ? min2 : min1) << sh);
+                for (int r = 0; r < R; ++r) {
+                    const int i = lane + 32 * (R * c + r);
+                    const uint32_t G2 = acc[r], UC2 = UC[i];
+                    const uint2 ta = TA[i];
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int n = i + half * H;
+                        const int G = (int)((G2 >> (16 * half)) & 0xffffu);
+                        const int uc = (int)((UC2 >> (16 * half)) & 0xffffu);
+                        const int tc = (int)((ta.x >> (16 * half)) & 0xffffu);
+                        const int a = (int)((ta.y >> (16 * half)) & 0xffffu);
+                        const int E = (G - bias + 2 * uc - tc) * 256 - P.alpha_q * a;
+                        if (E > P.theta_q && n < Z) {
+                            const uint32_t blk = div_small((uint32_t)n, P.p, P.p_magic);
+                            const unsigned long long key =
+                                ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - (uint32_t)n);
+                            atomicMax(&keys[blk], key);
                         }
                     }
                 }
             }
             __syncwarp();
-            // metric and per-block candidates
-            for (int i = lane; i < H; i += 32) {
-                const uint32_t U2 = UP[i];
-                if (U2 == 0u) continue;  // U = 0 gives E' <= 0: never a candidate
-                UP[i] = 0u;
-                const uint32_t T2 = BT[i];
-                for (int half = 0; half < 2; ++half) {
-                    const int n = i + half * H;
-                    const int U = (int)((U2 >> (16 * half)) & 0xffffu);
-                    if (U == 0 || n >= Z) continue;
-                    const int tot = (int)((T2 >> (16 * half)) & 0xffffu);
-                    const int E = (2 * U - tot) * 256 - P.alpha_q * abs((int)q[n]);
-                    if (E > P.theta_q) {
-                        const uint32_t blk = div_small((uint32_t)n, P.p, P.p_magic);
-                        const unsigned long long key =
-                            ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - (uint32_t)n);
-                        atomicMax(&keys[blk], key);
-                    }
-                }
-            }
-            __syncwarp();
-            // flips: the warp toggles the checks of one flipped bit at a time
+            // flips: the warp toggles the checks of one flipped bit at a time and
+            // keeps the syndrome, the doubled V array and the corrections current
             int dW = 0, nflip = 0;
             for (int b0 = 0; b0 < P.B; b0 += 32) {
                 const int b = b0 + lane;
@@ -357,12 +306,23 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
                     const uint32_t n = 0xffffffffu - (uint32_t)__shfl_sync(FULL, key, src);
                     if (lane == 0) zbits[n >> 5] ^= 1u << (n & 31);
                     for (int e = lane; e < DC; e += 32) {
-                        uint32_t m = n + u_off[e];
+                        uint32_t m = n + (e < 32 ? my_u : u_off[e]);
                         m = m >= (uint32_t)Z ? m - Z : m;
                         const uint32_t bit = 1u << (m & 31);
                         const uint32_t old = atomicXor(&sbits[m >> 5], bit);
-                        dW += (old & bit) ? -1 : 1;
-                        atomicXor(&Vw[m >> 1], (crec[m] & 0x7fu) << (16 * (m & 1)));
+                        const bool now_set = !(old & bit);
+                        dW += now_set ? 1 : -1;
+                        const uint32_t rec = crec[m];
+                        const uint32_t min1 = rec & 0x7fu, diff = ((rec >> 8) & 0x7fu) - min1;
+                        doubled_add(X2, (int)m, now_set ? 2 * (int)min1 : -2 * (int)min1, Z, H, XJ);
+                        if (diff) {
+                            int ns = (int)m + (int)d_off[rec >> 16];
+                            ns = ns >= Z ? ns - Z : ns;
+                            int idx, sh;
+                            pair_slot(ns, H, idx, sh);
+                            const uint32_t d = diff << sh;
+                            atomicAdd(&UC[idx], now_set ? d : (0u - d));
+                        }
                     }
                 }
             }
@@ -427,7 +387,6 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     P.out_bits = out_bits;
     P.out_iters = out_iters;
     P.counter = counter;
-    P.dense_above = 128;
 
     const uint32_t Z = c->Z, H = P.H;
     uint32_t o = align16(Z + 32);
@@ -435,12 +394,10 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     o += align16(4 * (Z + H));
     P.off_crec = o;
     o += align16(4 * Z);
-    P.off_BT = o;
+    P.off_TA = o;
+    o += align16(8 * H);
+    P.off_UC = o;
     o += align16(4 * H);
-    P.off_UP = o;
-    o += align16(4 * H);
-    P.off_V = o;
-    o += align16(2 * (Z + 1));
     P.off_s = o;
     o += align16(4 * ((Z + 31) / 32));
     P.off_z = o;
