@@ -20,9 +20,10 @@
 //           = sum_{m in M(n)} V'_m - 128 d_c + 2 UC_n - TC_n,
 //     V'_m = (2 s_m - 1) min1_m + 128 (in [1, 255], so packed sums never carry),
 //     TC_n = sum of diff_m over the checks whose arg-min bit is n (fixed) and
-//     UC_n = the same sum over those checks with s_m = 1.  The sum over M(n)
+//     UC_n = the same sum over those checks with s_m = 1; the kernel keeps
+//     SC_n = 2 UC_n - TC_n = sum of (2 s_m - 1) diff_m over those checks.  The sum over M(n)
 //     is a gather over the doubled array of V': one load and one packed add per
-//     two edges.  Every syndrome toggle updates V' (+-2 min1) and UC (+-diff)
+//     two edges.  Every syndrome toggle updates V' (+-2 min1) and SC (+-2 diff)
 //     in place, so a pass is one gather plus its metric epilogue.
 //   * E'_n = 256 D_n - alpha_q a_n (Eq. 1 times 256); block arg-max, flips and
 //     the no-flip shortcut are those of the generic decoder.
@@ -47,7 +48,7 @@ struct CyclicParams {
     uint32_t *out_bits;
     int32_t *out_iters;
     unsigned long long *counter;
-    uint32_t warp_bytes, off_X, off_crec, off_TA, off_UC, off_s, off_z, off_keys;
+    uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys;
 };
 
 __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
@@ -120,9 +121,9 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
     int8_t *stage = reinterpret_cast<int8_t *>(ws);
     uint32_t *X2 = reinterpret_cast<uint32_t *>(ws + P.off_X);
     uint32_t *crec = reinterpret_cast<uint32_t *>(ws + P.off_crec);
-    uint2 *TA = reinterpret_cast<uint2 *>(ws + P.off_TA);  // (tot pair, |q| pair) per position pair
-    uint32_t *TAw = reinterpret_cast<uint32_t *>(TA);
-    uint32_t *UC = reinterpret_cast<uint32_t *>(ws + P.off_UC);
+    // SC_n = sum of (2 s_m - 1) diff_m over the checks whose arg-min bit is n,
+    // packed in pairs, each half biased by 0x4000 (|SC| <= 127 d_c < 0x4000)
+    uint32_t *SC = reinterpret_cast<uint32_t *>(ws + P.off_SC);
     uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
     const uintptr_t ybase = reinterpret_cast<uintptr_t>(P.y);
     const uintptr_t yend = ybase + (uintptr_t)(P.F * (int64_t)Z);
     const uint32_t my_u = lane < DC ? u_off[lane] : 0u;  // column offset of row position e = lane
-    const int bias = 128 * DC;
+    const int bias = 128 * DC + 0x4000;
 
     for (int b = lane; b < P.B; b += 32) keys[b] = 0ull;
 
@@ -165,11 +166,7 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
         }
         __syncwarp();
         const int8_t *q = stage + off;
-        for (int i = lane; i < H; i += 32) {
-            const int n1 = i + H < Z ? i + H : i + H - Z;
-            UC[i] = 0u;
-            TA[i] = make_uint2(0u, (uint32_t)abs((int)q[i]) | ((uint32_t)abs((int)q[n1]) << 16));
-        }
+        for (int i = lane; i < H; i += 32) SC[i] = 0x40004000u;
 
         for (int w = 0; w < Zw; ++w) {
             const int n = (w << 5) + lane;
@@ -180,7 +177,7 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
         __syncwarp();
 
         // ---- check pass: min1/pos, min2 and parity of every check pair; the
-        //      arg-min corrections of tot (into TA.x) and of U (into UC) ------
+        //      signed arg-min corrections (into SC) ----------------------------
         int W = 0;
         for (int c = 0; c < chunks; ++c) {
             uint32_t k1[R], k2[R], par[R];
@@ -214,15 +211,15 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
                     const int m = i + half * H;
                     const uint32_t a1 = k1[r] >> (16 * half), a2 = k2[r] >> (16 * half);
                     const uint32_t min1 = (a1 >> 8) & 0x7fu, pos = a1 & 0x7fu, min2 = (a2 >> 8) & 0x7fu;
-                    crec[m] = min1 | (min2 << 8) | (pos << 16);
                     const uint32_t diff = min2 - min1;
+                    int n = m + (int)d_off[pos];
+                    n = n >= Z ? n - Z : n;
+                    crec[m] = min1 | (diff << 8) | ((uint32_t)n << 16);  // min1, diff, arg-min bit
                     if (diff) {
-                        int n = m + (int)d_off[pos];
-                        n = n >= Z ? n - Z : n;
                         int idx, sh;
                         pair_slot(n, H, idx, sh);
-                        atomicAdd(&TAw[2 * idx], diff << sh);
-                        if (half ? s_hi : s_lo) atomicAdd(&UC[idx], diff << sh);
+                        const int d = (half ? s_hi : s_lo) ? (int)diff : -(int)diff;
+                        atomicAdd(&SC[idx], sh ? (uint32_t)d * 65536u : (uint32_t)d);
                     }
                 }
                 const uint32_t slo = __ballot_sync(FULL, s_lo);
@@ -268,16 +265,14 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
                 }
                 for (int r = 0; r < R; ++r) {
                     const int i = lane + 32 * (R * c + r);
-                    const uint32_t G2 = acc[r], UC2 = UC[i];
-                    const uint2 ta = TA[i];
+                    const uint32_t G2 = acc[r], SC2 = SC[i];
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         const int n = i + half * H;
                         const int G = (int)((G2 >> (16 * half)) & 0xffffu);
-                        const int uc = (int)((UC2 >> (16 * half)) & 0xffffu);
-                        const int tc = (int)((ta.x >> (16 * half)) & 0xffffu);
-                        const int a = (int)((ta.y >> (16 * half)) & 0xffffu);
-                        const int E = (G - bias + 2 * uc - tc) * 256 - P.alpha_q * a;
+                        const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
+                        const int a = abs((int)q[n < Z ? n : 0]);
+                        const int E = (G + sc - bias) * 256 - P.alpha_q * a;
                         if (E > P.theta_q && n < Z) {
                             const uint32_t blk = div_small((uint32_t)n, P.p, P.p_magic);
                             const unsigned long long key =
@@ -313,15 +308,13 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
                         const bool now_set = !(old & bit);
                         dW += now_set ? 1 : -1;
                         const uint32_t rec = crec[m];
-                        const uint32_t min1 = rec & 0x7fu, diff = ((rec >> 8) & 0x7fu) - min1;
+                        const uint32_t min1 = rec & 0x7fu, diff = (rec >> 8) & 0x7fu;
                         doubled_add(X2, (int)m, now_set ? 2 * (int)min1 : -2 * (int)min1, Z, H, XJ);
                         if (diff) {
-                            int ns = (int)m + (int)d_off[rec >> 16];
-                            ns = ns >= Z ? ns - Z : ns;
                             int idx, sh;
-                            pair_slot(ns, H, idx, sh);
-                            const uint32_t d = diff << sh;
-                            atomicAdd(&UC[idx], now_set ? d : (0u - d));
+                            pair_slot((int)(rec >> 16), H, idx, sh);
+                            const int d = now_set ? 2 * (int)diff : -2 * (int)diff;
+                            atomicAdd(&SC[idx], sh ? (uint32_t)d * 65536u : (uint32_t)d);
                         }
                     }
                 }
@@ -394,9 +387,7 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     o += align16(4 * (Z + H));
     P.off_crec = o;
     o += align16(4 * Z);
-    P.off_TA = o;
-    o += align16(8 * H);
-    P.off_UC = o;
+    P.off_SC = o;
     o += align16(4 * H);
     P.off_s = o;
     o += align16(4 * ((Z + 31) / 32));
