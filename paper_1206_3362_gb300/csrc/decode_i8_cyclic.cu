@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
     const uintptr_t yend = ybase + (uintptr_t)(P.F * (int64_t)Z);
     const uint32_t my_u = lane < DC ? u_off[lane] : 0u;  // column offset of row position e = lane
     const int bias = 128 * DC + 0x4000;
+    const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
 
     for (int b = lane; b < P.B; b += 32) keys[b] = 0ull;
 
@@ -258,14 +259,25 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
 #pragma unroll
                 for (int r = 0; r < R; ++r) acc[r] = 0u;
                 const uint32_t *xb = X2 + lane + 32 * R * c;
-                for (int e = 0; e < DC; ++e) {
-                    const uint32_t *p = xb + u_off[e];
+                int e = 0;
+                for (; e + 1 < DC; e += 2) {
+                    const uint32_t *p0 = xb + u_off[e];
+                    const uint32_t *p1 = xb + u_off[e + 1];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r] += p[32 * r];
+                    for (int r = 0; r < R; ++r) acc[r] += p0[32 * r] + p1[32 * r];
+                }
+                if (e < DC) {
+                    const uint32_t *p0 = xb + u_off[e];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += p0[32 * r];
                 }
                 for (int r = 0; r < R; ++r) {
                     const int i = lane + 32 * (R * c + r);
                     const uint32_t G2 = acc[r], SC2 = SC[i];
+                    // D_n >= 1 is necessary for E' > theta >= 0: test both halves of
+                    // G + SC at once (0x8000 + (G + SC - bias) - 1 has bit 15 set iff
+                    // D_n >= 1; the half-words stay in [0, 65535])
+                    if (((G2 + SC2 + dfilter) & 0x80008000u) == 0u) continue;
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         const int n = i + half * H;
