@@ -182,14 +182,17 @@ def main():
     from paper_1206_3362_gb300 import fwbf
     from paper_1206_3362_gb300.inputs import Encoder, make_code
     from paper_1206_3362_gb300.inputs.channel import bpsk_awgn_torch, random_codewords_torch
+    from paper_1206_3362_gb300.sharding import frame_seed, max_over_ranks
 
     w = WORKLOAD
     F = args.frames
     h = make_code(w["code"])
     enc = Encoder(h)
     E, N = h.nnz, h.N
-    _, c = random_codewords_torch(enc, F, seed=1000 + rank, device=dev)
-    y = bpsk_awgn_torch(c, w["ebn0_db"], enc.rate, seed=1000 + rank).contiguous()
+    # weak scaling: every rank makes and decodes its own batch of F frames
+    seed = frame_seed(1000, rank)
+    _, c = random_codewords_torch(enc, F, seed=seed, device=dev)
+    y = bpsk_awgn_torch(c, w["ebn0_db"], enc.rate, seed=seed).contiguous()
     code = fwbf.Code.from_parity_check(h, w["seg_len"])
     B = code.info.n_blocks
     q = torch.empty((F, N), dtype=torch.int8, device=dev)
@@ -225,10 +228,7 @@ def main():
         dist.barrier()
     ms = t_start.elapsed_time(t_end)
     dec_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, device=dev)
     assert fwbf.fwbf_last_status(stream) == 0
 
     info_bits = F * enc.K * world * args.steps
