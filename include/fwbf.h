@@ -146,6 +146,86 @@ int fwbf_decode_f32(fwbf_code c, const float *y, int64_t n_frames, int32_t max_i
 int fwbf_metric_f32(fwbf_code c, const float *y, int64_t n_frames, float alpha, float *out_E,
                     void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Per-pass schedules and the learned schedule                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The weighting factor alpha of Eq. 1 and the flip threshold of Sec. III
+ * Step 2 (0 in the paper: flip iff E_b > 0) are the method's only parameters;
+ * these entry points vary them per pass.  Both need a cyclic code (a single
+ * circulant H, e.g. the EG(2,2^s) codes); other codes give FWBF_EUNSUPPORTED.
+ *
+ * Per-pass features (float [8], also what the learned network reads), for the
+ * state at the start of pass k of a frame:
+ *   0 W_k / N    1 W_{k-1} / N (W_0 at k = 0)    2 W_0 / N    3 k / 16
+ *   4 flips of pass k-1 / n_blocks (0 at k = 0)
+ *   5 bits with sum_m (2 s_m - 1) w_{n,m} >= 1 at pass k-1, / N (0 at k = 0)
+ *   6 mean |q_n| / 127                            7 fraction of |q_n| < 8
+ * (W_k: syndrome weight, N = M for a cyclic code.)
+ */
+#define FWBF_MLP_IN 8
+#define FWBF_MLP_HIDDEN 64
+#define FWBF_MLP_OUT 2
+#define FWBF_MLP_PARAMS 4866
+#define FWBF_MLP_BLOB_BYTES 10000
+
+/*
+ * fwbf_decode with alpha_q / theta_q (x256 fixed point, as alpha_q of
+ * fwbf_decode) of pass k of frame f read from device arrays at
+ * [f * sched_stride + k], k < max_iter (sched_stride = 0: one schedule for all
+ * frames).  Values are clamped to alpha_q in [0, 16384], theta_q >= 0.  The
+ * no-flip shortcut is not used (a later pass may use other parameters).
+ *   out_feat    device float [n_frames][feat_passes][8] or NULL: the features
+ *               above at the start of every pass k < feat_passes (unwritten for
+ *               passes a frame does not run).
+ */
+int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter,
+                      const int32_t *alpha_q, const int32_t *theta_q, int64_t sched_stride,
+                      uint32_t *out_bits, int32_t *out_iters, float *out_feat,
+                      int32_t feat_passes, void *stream);
+
+/*
+ * FWBF whose pass parameters come from the learned network, with plain FWBF
+ * as the fallback.  For pass k < k_learn the decoding warp evaluates the
+ * network on the features above: outputs (o0, o1) give alpha = o0 and
+ * theta = 16 o1 (in units of the int8 metric; theta_q = rne(256 theta)),
+ * clamped to [0, 64] and [0, 4096].  A frame whose syndrome is not zero after
+ * k_learn passes is decoded again from its channel values by plain FWBF
+ * (alpha_fallback, threshold 0, max_iter passes); its pass count is then
+ * k_learn + the fallback's passes (or -max_iter if the fallback fails too).
+ *   mlp          device weight blob, FWBF_MLP_BLOB_BYTES, 16-byte aligned:
+ *                W1 bf16[64][8] | W2 bf16[64][64] | W3 bf16[2][64] |
+ *                b1 f32[64] | b2 f32[64] | b3 f32[2]  (bytes 0, 1024, 9216,
+ *                9472, 9728, 9984)
+ *   out_sched    device int32 [n_frames][k_learn][2] or NULL: the (alpha_q,
+ *                theta_q) used in every learned pass that ran
+ *   out_feat, feat_passes   as fwbf_decode_sched
+ */
+int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter,
+                        int32_t k_learn, float alpha_fallback, const void *mlp,
+                        uint32_t *out_bits, int32_t *out_iters, int32_t *out_sched,
+                        float *out_feat, int32_t feat_passes, void *stream);
+
+/*
+ * Training kernels of the network (float32 master parameters in the blob's
+ * order: W1, W2, W3, b1, b2, b3, FWBF_MLP_PARAMS floats, device).
+ *   fwbf_mlp_pack     master -> blob (weights rounded to bf16)
+ *   fwbf_mlp_forward  out[n][2] = network(x[n][8]) with the blob's weights
+ *   fwbf_mlp_grad     adds to grad the gradient, with respect to the blob's
+ *                     weights, of sum over the n samples of
+ *                     ||network(x_s) - target_s||^2 / n_total, and that sum to
+ *                     *loss (device float)
+ *   fwbf_mlp_adam     one Adam step (step >= 1) on master with grad; rewrites
+ *                     the blob and clears grad
+ */
+int fwbf_mlp_pack(const float *master, void *blob, void *stream);
+int fwbf_mlp_forward(const void *blob, const float *x, int64_t n, float *out, void *stream);
+int fwbf_mlp_grad(const void *blob, const float *x, const float *target, int64_t n, int64_t n_total,
+                  float *grad, float *loss, void *stream);
+int fwbf_mlp_adam(float *master, void *blob, float *grad, float *m, float *v, int64_t step,
+                  float lr, float beta1, float beta2, float eps, void *stream);
+
 /*
  * Waits for the stream, then reports and clears the device status word that
  * kernels set when a bounded wait runs out: FWBF_OK or FWBF_ETIMEOUT.

@@ -30,10 +30,14 @@
 // All integer results equal the definition (Sec. III, Eq. 1) exactly.
 #include "device_common.cuh"
 #include "fwbf_internal.h"
+#include "mlp_device.cuh"
 
 namespace fwbf {
 
 __device__ int g_status_i8_cyclic;
+
+constexpr int kModePlain = 0, kModeSched = 1, kModeLearned = 2;
+constexpr int kFeatures = FWBF_MLP_IN;
 
 struct CyclicParams {
     const uint32_t *table;
@@ -48,6 +52,16 @@ struct CyclicParams {
     uint32_t *out_bits;
     int32_t *out_iters;
     unsigned long long *counter;
+    // per-pass schedule (kModeSched): alpha_q / theta_q of pass k of frame f at [f * sched_stride + k]
+    int mode;
+    const int32_t *sched_a, *sched_t;
+    long long sched_stride;
+    // learned schedule (kModeLearned): network, learned passes, recorded schedule
+    const unsigned char *mlp;
+    int k_learn;
+    int32_t *out_sched;   // [F][k_learn][2] (alpha_q, theta_q) used, or null
+    float *out_feat;      // [F][feat_passes][kFeatures] features per pass, or null
+    int feat_passes;
     uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys;
 };
 
@@ -167,6 +181,20 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
         }
         __syncwarp();
         const int8_t *q = stage + off;
+        // frame statistics for the features of scheduled and learned decoding
+        float mean_a = 0.0f, weak_frac = 0.0f;
+        if (P.mode != kModePlain || P.out_feat) {
+            int sa = 0, sw = 0;
+            for (int n = lane; n < Z; n += 32) {
+                const int a = abs((int)q[n]);
+                sa += a;
+                sw += a < 8;
+            }
+            mean_a = (float)warp_sum(sa) / (127.0f * (float)Z);
+            weak_frac = (float)warp_sum(sw) / (float)Z;
+        }
+        int iters = 0, passes_before = 0, mode = P.mode;
+        for (;;) {  // attempts: the requested mode, then plain FWBF as fallback
         for (int i = lane; i < H; i += 32) SC[i] = 0x40004000u;
 
         for (int w = 0; w < Zw; ++w) {
@@ -242,16 +270,60 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
         __syncwarp();
 
         // ---- iterations ------------------------------------------------------
-        int iters;
+        const int W0 = W;
+        int Wprev = W, nflip_prev = 0, ncand_prev = 0;
+        bool give_up = false;  // learned passes exhausted: fall back to plain FWBF
         for (int k = 0;; ++k) {
             if (W == 0) {
-                iters = k;
+                iters = passes_before + k;
+                break;
+            }
+            if (mode == kModeLearned && k == P.k_learn) {
+                give_up = true;
                 break;
             }
             if (k == P.max_iter) {
                 iters = -P.max_iter;
                 break;
             }
+            // weighting factor and threshold of this pass (fixed point, x256)
+            int aq = P.alpha_q, tq = P.theta_q;
+            if (mode != kModePlain || P.out_feat) {
+                float feat[kFeatures];
+                feat[0] = (float)W / (float)Z;
+                feat[1] = (float)Wprev / (float)Z;
+                feat[2] = (float)W0 / (float)Z;
+                feat[3] = (float)k * (1.0f / 16.0f);
+                feat[4] = (float)nflip_prev / (float)P.B;
+                feat[5] = (float)ncand_prev / (float)Z;
+                feat[6] = mean_a;
+                feat[7] = weak_frac;
+                const int kk = passes_before + k;
+                if (P.out_feat && kk < P.feat_passes && lane == 0) {
+                    float *o = P.out_feat + (f * (unsigned long long)P.feat_passes + kk) * kFeatures;
+#pragma unroll
+                    for (int j = 0; j < kFeatures; ++j) o[j] = feat[j];
+                }
+                if (mode == kModeSched) {
+                    const long long o = (long long)f * P.sched_stride + kk;
+                    aq = P.sched_a[o];
+                    tq = P.sched_t[o];
+                } else if (mode == kModeLearned) {
+                    float al, th;
+                    mlp_eval(P.mlp, feat, lane, al, th);
+                    th *= 16.0f;
+                    aq = __float2int_rn(fminf(fmaxf(al, 0.0f), 64.0f) * 256.0f);
+                    tq = __float2int_rn(fminf(fmaxf(th, 0.0f), 4096.0f) * 256.0f);
+                    if (P.out_sched && lane == 0) {
+                        const unsigned long long o = (f * (unsigned long long)P.k_learn + k) * 2;
+                        P.out_sched[o] = aq;
+                        P.out_sched[o + 1] = tq;
+                    }
+                }
+                aq = min(max(aq, 0), 16384);
+                tq = max(tq, 0);
+            }
+            int ncand = 0;
             // D_n = sum (2 s_m - 1) w_{n,m} = G_n - 128 d_c + 2 UC_n - TC_n with
             // G the gather of V' over M(n); metric E' = 256 D_n - alpha_q a_n
             for (int c = 0; c < chunks; ++c) {
@@ -277,15 +349,18 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
                     // D_n >= 1 is necessary for E' > theta >= 0: test both halves of
                     // G + SC at once (0x8000 + (G + SC - bias) - 1 has bit 15 set iff
                     // D_n >= 1; the half-words stay in [0, 65535])
-                    if (((G2 + SC2 + dfilter) & 0x80008000u) == 0u) continue;
+                    uint32_t cmask = (G2 + SC2 + dfilter) & 0x80008000u;
+                    if (i + H >= Z) cmask &= 0x8000u;  // the duplicated position
+                    if (cmask == 0u) continue;
+                    ncand += __popc(cmask);
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         const int n = i + half * H;
                         const int G = (int)((G2 >> (16 * half)) & 0xffffu);
                         const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
                         const int a = abs((int)q[n < Z ? n : 0]);
-                        const int E = (G + sc - bias) * 256 - P.alpha_q * a;
-                        if (E > P.theta_q && n < Z) {
+                        const int E = (G + sc - bias) * 256 - aq * a;
+                        if (E > tq && n < Z) {
                             const uint32_t blk = div_small((uint32_t)n, P.p, P.p_magic);
                             const unsigned long long key =
                                 ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - (uint32_t)n);
@@ -331,13 +406,20 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
                     }
                 }
             }
+            Wprev = W;
             W += warp_sum(dW);
+            nflip_prev = nflip;
+            ncand_prev = warp_sum(ncand);
             __syncwarp();
-            if (nflip == 0) {
+            if (nflip == 0 && mode == kModePlain) {  // fixed point: every later pass repeats this one
                 iters = -P.max_iter;
                 break;
             }
         }
+        if (!give_up) break;
+        passes_before = P.k_learn;
+        mode = kModePlain;
+        }  // attempts
 
         uint32_t *ob = P.out_bits + f * (unsigned long long)Zw;
         for (int w = lane; w < Zw; w += 32) __stcs(ob + w, zbits[w]);
@@ -372,8 +454,19 @@ int read_and_clear_status_i8_cyclic(cudaStream_t s, int *out) {
 
 int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
                             int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
-                            cudaStream_t s) {
+                            cudaStream_t s, const CyclicModes *modes) {
     CyclicParams P{};
+    if (modes) {
+        P.mode = modes->mode;
+        P.sched_a = modes->sched_a;
+        P.sched_t = modes->sched_t;
+        P.sched_stride = modes->sched_stride;
+        P.mlp = modes->mlp;
+        P.k_learn = modes->k_learn;
+        P.out_sched = modes->out_sched;
+        P.out_feat = modes->out_feat;
+        P.feat_passes = modes->feat_passes;
+    }
     P.table = c->d_table;
     P.table_words = c->table_words;
     P.rent_off = c->rent_off;
@@ -439,6 +532,31 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "decode_i8_cyclic launch");
+    return 0;
+}
+
+}  // namespace fwbf
+
+namespace fwbf {
+
+// Scheduled and learned decoding: the cyclic kernel with a frame counter from
+// the stream-ordered allocator.
+int launch_decode_i8_modes(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                           uint32_t *out_bits, int32_t *out_iters, const CyclicModes &modes, cudaStream_t s) {
+    if (!cyclic_eligible(c)) return fail(FWBF_EUNSUPPORTED, "per-pass schedules need a cyclic code");
+    unsigned long long *counter = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(counter, s);
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    const int rc = launch_decode_i8_cyclic(c, y, n_frames, max_iter, alpha_q, 0, out_bits, out_iters, counter, s,
+                                           &modes);
+    e = cudaFreeAsync(counter, s);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(frame counter)");
     return 0;
 }
 

@@ -257,6 +257,49 @@ int fwbf_decode_noalloc(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
                                     static_cast<cudaStream_t>(stream));
 }
 
+int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, const int32_t *alpha_q,
+                      const int32_t *theta_q, int64_t sched_stride, uint32_t *out_bits, int32_t *out_iters,
+                      float *out_feat, int32_t feat_passes, void *stream) {
+    int rc = check_decode_args(c, y, n_frames, max_iter, 1.0f, out_bits, out_iters);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
+    if (n_frames > 0 && (!alpha_q || !theta_q)) return fail(FWBF_EINVAL, "schedule is NULL");
+    if (sched_stride != 0 && sched_stride < max_iter) return fail(FWBF_EINVAL, "sched_stride < max_iter");
+    if (out_feat && feat_passes < 1) return fail(FWBF_EINVAL, "feat_passes < 1");
+    if (n_frames == 0) return FWBF_OK;
+    CyclicModes m;
+    m.mode = 1;
+    m.sched_a = alpha_q;
+    m.sched_t = theta_q;
+    m.sched_stride = sched_stride;
+    m.out_feat = out_feat;
+    m.feat_passes = out_feat ? feat_passes : 0;
+    return launch_decode_i8_modes(c, y, n_frames, max_iter, 0, out_bits, out_iters, m,
+                                  static_cast<cudaStream_t>(stream));
+}
+
+int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, int32_t k_learn,
+                        float alpha_fallback, const void *mlp, uint32_t *out_bits, int32_t *out_iters,
+                        int32_t *out_sched, float *out_feat, int32_t feat_passes, void *stream) {
+    int rc = check_decode_args(c, y, n_frames, max_iter, alpha_fallback, out_bits, out_iters);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
+    if (k_learn < 1) return fail(FWBF_EINVAL, "k_learn must be >= 1");
+    if (!mlp || reinterpret_cast<uintptr_t>(mlp) % 16) return fail(FWBF_EINVAL, "mlp blob NULL or unaligned");
+    if (out_feat && feat_passes < 1) return fail(FWBF_EINVAL, "feat_passes < 1");
+    if (n_frames == 0) return FWBF_OK;
+    CyclicModes m;
+    m.mode = 2;
+    m.mlp = static_cast<const unsigned char *>(mlp);
+    m.k_learn = k_learn;
+    m.out_sched = out_sched;
+    m.out_feat = out_feat;
+    m.feat_passes = out_feat ? feat_passes : 0;
+    const int aq = (int)nearbyint((double)alpha_fallback * 256.0);
+    return launch_decode_i8_modes(c, y, n_frames, max_iter, aq, out_bits, out_iters, m,
+                                  static_cast<cudaStream_t>(stream));
+}
+
 int fwbf_decode_f32(fwbf_code c, const float *y, int64_t n_frames, int32_t max_iter, float alpha,
                     uint32_t *out_bits, int32_t *out_iters, void *stream) {
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);

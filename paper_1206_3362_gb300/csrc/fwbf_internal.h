@@ -48,9 +48,23 @@ int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, in
                      cudaStream_t s);
 bool cyclic_eligible(const fwbf_code_s *c);
 int read_and_clear_status_i8_cyclic(cudaStream_t s, int *out);
+// per-pass parameters of the cyclic decoder (mode 0: fixed, 1: schedule arrays,
+// 2: learned network with plain fallback)
+struct CyclicModes {
+    int mode = 0;
+    const int32_t *sched_a = nullptr, *sched_t = nullptr;
+    long long sched_stride = 0;
+    const unsigned char *mlp = nullptr;
+    int k_learn = 0;
+    int32_t *out_sched = nullptr;
+    float *out_feat = nullptr;
+    int feat_passes = 0;
+};
 int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
                             int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
-                            cudaStream_t s);
+                            cudaStream_t s, const CyclicModes *modes = nullptr);
+int launch_decode_i8_modes(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                           uint32_t *out_bits, int32_t *out_iters, const CyclicModes &modes, cudaStream_t s);
 int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
                              int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
                              cudaStream_t s);

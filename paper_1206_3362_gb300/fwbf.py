@@ -58,6 +58,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_decode_noalloc": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_decode_f32": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
+        "fwbf_decode_sched": ([P, P, i64, i32, P, P, i64, P, P, P, i32, P], ctypes.c_int),
+        "fwbf_decode_learned": ([P, P, i64, i32, i32, f32, P, P, P, P, P, i32, P], ctypes.c_int),
+        "fwbf_mlp_pack": ([P, P, P], ctypes.c_int),
+        "fwbf_mlp_forward": ([P, P, i64, P, P], ctypes.c_int),
+        "fwbf_mlp_grad": ([P, P, P, i64, i64, P, P, P], ctypes.c_int),
+        "fwbf_mlp_adam": ([P, P, P, P, P, i64, f32, f32, f32, f32, P], ctypes.c_int),
         "fwbf_last_status": ([P], ctypes.c_int),
         "fwbf_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "fwbf_last_error": ([], ctypes.c_char_p),
@@ -179,6 +185,82 @@ def fwbf_metric_f32(code, y, alpha: float, out_E, stream=None) -> None:
     F = _frames(y, info.N)
     _check(load_library().fwbf_metric_f32(code, _dev(y, torch.float32, "y"), F, float(alpha),
                                           _dev(out_E, torch.float32, "out_E"), _stream(stream)))
+
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS, MLP_BLOB_BYTES = 8, 64, 2, 4866, 10000
+
+
+def _opt(t, dtype, name):
+    return None if t is None else _dev(t, dtype, name)
+
+
+def fwbf_decode_sched(code, y, max_iter: int, alpha_q, theta_q, out_bits, out_iters, out_feat=None,
+                      stream=None) -> None:
+    """Per-pass schedule: alpha_q/theta_q int32 CUDA tensors [n_frames][max_iter]
+    (or [max_iter], shared by all frames); out_feat float32 [n_frames][P][8]."""
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y, info.N)
+    stride = max_iter if alpha_q.dim() == 2 else 0
+    if alpha_q.shape != theta_q.shape or alpha_q.shape[-1] != max_iter:
+        raise ValueError("schedules must be [n_frames][max_iter] or [max_iter]")
+    fp = out_feat.shape[1] if out_feat is not None else 0
+    _check(load_library().fwbf_decode_sched(code, _dev(y, torch.int8, "y"), F, int(max_iter),
+                                            _dev(alpha_q, torch.int32, "alpha_q"), _dev(theta_q, torch.int32, "theta_q"),
+                                            stride, _dev(out_bits, torch.int32, "out_bits"),
+                                            _dev(out_iters, torch.int32, "out_iters"),
+                                            _opt(out_feat, torch.float32, "out_feat"), fp, _stream(stream)))
+
+
+def fwbf_decode_learned(code, y, max_iter: int, k_learn: int, alpha_fallback: float, mlp_blob, out_bits,
+                        out_iters, out_sched=None, out_feat=None, stream=None) -> None:
+    """Learned per-pass schedule (network blob: uint8 CUDA tensor of
+    MLP_BLOB_BYTES), plain FWBF fallback after k_learn passes."""
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y, info.N)
+    fp = out_feat.shape[1] if out_feat is not None else 0
+    _check(load_library().fwbf_decode_learned(code, _dev(y, torch.int8, "y"), F, int(max_iter), int(k_learn),
+                                              float(alpha_fallback), _dev(mlp_blob, torch.uint8, "mlp_blob"),
+                                              _dev(out_bits, torch.int32, "out_bits"),
+                                              _dev(out_iters, torch.int32, "out_iters"),
+                                              _opt(out_sched, torch.int32, "out_sched"),
+                                              _opt(out_feat, torch.float32, "out_feat"), fp, _stream(stream)))
+
+
+def fwbf_mlp_pack(master, blob, stream=None) -> None:
+    import torch
+
+    _check(load_library().fwbf_mlp_pack(_dev(master, torch.float32, "master"), _dev(blob, torch.uint8, "blob"),
+                                        _stream(stream)))
+
+
+def fwbf_mlp_forward(blob, x, out, stream=None) -> None:
+    import torch
+
+    _check(load_library().fwbf_mlp_forward(_dev(blob, torch.uint8, "blob"), _dev(x, torch.float32, "x"), x.shape[0],
+                                           _dev(out, torch.float32, "out"), _stream(stream)))
+
+
+def fwbf_mlp_grad(blob, x, target, n_total: int, grad, loss, stream=None) -> None:
+    import torch
+
+    _check(load_library().fwbf_mlp_grad(_dev(blob, torch.uint8, "blob"), _dev(x, torch.float32, "x"),
+                                        _dev(target, torch.float32, "target"), x.shape[0], int(n_total),
+                                        _dev(grad, torch.float32, "grad"), _dev(loss, torch.float32, "loss"),
+                                        _stream(stream)))
+
+
+def fwbf_mlp_adam(master, blob, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8,
+                  stream=None) -> None:
+    import torch
+
+    _check(load_library().fwbf_mlp_adam(_dev(master, torch.float32, "master"), _dev(blob, torch.uint8, "blob"),
+                                        _dev(grad, torch.float32, "grad"), _dev(m, torch.float32, "m"),
+                                        _dev(v, torch.float32, "v"), int(step), float(lr), float(beta1),
+                                        float(beta2), float(eps), _stream(stream)))
 
 
 def fwbf_last_status(stream=None) -> int:
