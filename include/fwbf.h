@@ -147,6 +147,56 @@ int fwbf_metric_f32(fwbf_code c, const float *y, int64_t n_frames, float alpha, 
                     void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Batched decoding of several codes in one persistent launch               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper decodes one code at a time; this is a throughput form of the same
+ * decoder (results are those of fwbf_decode for every job): codes of
+ * different N, M and row / column weight, each with its own frames and
+ * outputs, share one persistent kernel launch.
+ */
+typedef struct fwbf_batch_s *fwbf_batch;
+
+typedef struct {
+    fwbf_code code;        /* code handle (its seg_len p is used) */
+    const int8_t *y;       /* device int8 [n_frames][N], 16-byte aligned */
+    int64_t n_frames;      /* >= 0 */
+    int32_t max_iter;      /* >= 1 */
+    float alpha;           /* 0 <= alpha <= 64 */
+    uint32_t *out_bits;    /* device uint32 [n_frames][ceil(N/32)] */
+    int32_t *out_iters;    /* device int32 [n_frames] */
+} fwbf_batch_job;
+
+/*
+ * Builds a batch of 1..16 jobs (the descriptors are copied; buffers must stay
+ * valid while the batch is used).
+ *   warps_per_cta   1..16: warps (one frame each) per CTA of the launch
+ *   packed          1: cyclic codes use the packed two-positions-per-register
+ *                   decoder; 0: every code uses the list decoder
+ * Allocates the device job table and one frame counter per job (owned by the
+ * handle).  Errors: FWBF_EINVAL, FWBF_EUNSUPPORTED (a code too large for one
+ * warp's shared memory), FWBF_ENOMEM, FWBF_ECUDA.
+ */
+int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_per_cta,
+                      int32_t packed, fwbf_batch *out);
+
+/*
+ * Decodes every job of the batch: clears the job counters and queues one
+ * persistent launch on the stream.  It allocates nothing and does not
+ * synchronise, so the call can be captured into a CUDA graph and replayed
+ * (the buffers are those given at create time).  Calls of the same batch must
+ * not overlap on the GPU (they share the counters).
+ */
+int fwbf_decode_batch(fwbf_batch b, void *stream);
+
+/* Waits for the stream; FWBF_ETIMEOUT if a batch kernel gave up a bounded wait. */
+int fwbf_batch_status(void *stream);
+
+/* Releases a batch (waits for the device). NULL is a no-op. */
+int fwbf_batch_destroy(fwbf_batch b);
+
+/* ------------------------------------------------------------------------ */
 /* Per-pass schedules and the learned schedule                              */
 /* ------------------------------------------------------------------------ */
 

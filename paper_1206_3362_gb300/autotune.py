@@ -1,0 +1,149 @@
+"""Autotuner for the decoder's free parameters on the running GPU.
+
+Tuned per code, on seeded calibration frames at a chosen Eb/N0:
+
+* block length p of the partially parallel bit-choose and the weighting factor
+  alpha -- both change results, so a candidate is admitted only if it is
+  FER-qualified: on the same calibration frames it decodes at least as many
+  frames to the transmitted codeword as the reference setting (the paper's
+  p and alpha);
+* the decoder variant ("bit-packing width": the packed cyclic decoder with two
+  positions per 32-bit register, or the list decoder with one), and, for a
+  batch, the number of warps (frames in flight) per CTA.
+
+Among admitted settings the fastest (CUDA-event time of the decode) wins.
+Results are cached in a JSON file keyed by code, Eb/N0 and GPU name.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import fwbf
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "fwbf", "autotune.json")
+P_CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
+ALPHA_CANDIDATES = (1.0, 1.5, 2.0, 2.5)
+
+
+def code_key(h) -> str:
+    d = hashlib.sha1()
+    d.update(np.asarray([h.N, h.M], dtype=np.int64).tobytes())
+    d.update(np.asarray(h.rows, dtype=np.int32).tobytes())
+    d.update(np.asarray(h.cols, dtype=np.int32).tobytes())
+    return d.hexdigest()[:16]
+
+
+def _time(fn, reps=3):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def calibration_frames(h, enc, F, ebn0, seed, device="cuda"):
+    from .inputs.channel import bpsk_awgn_torch, random_codewords_torch
+
+    _, c = random_codewords_torch(enc, F, seed=seed, device=device)
+    y = bpsk_awgn_torch(c, ebn0, enc.rate, seed=seed).contiguous()
+    return fwbf.quantize(y), c
+
+
+def _frame_errors(bits, iters, c):
+    from .learned import frame_ok
+
+    return int((~frame_ok(bits, iters, c)).sum().item())
+
+
+def tune_code(h, enc, ebn0: float, p_ref: int, alpha_ref: float = 1.5, frames: int = 1 << 15,
+              max_iter: int = 100, p_candidates=P_CANDIDATES, alpha_candidates=ALPHA_CANDIDATES,
+              seed: int = 4242, log=None):
+    """Best FER-qualified (p, alpha) for one code; returns a dict with the
+    choice, the reference and every candidate measured."""
+    q, c = calibration_frames(h, enc, frames, ebn0, seed)
+    results = []
+    ref = None
+    cands = sorted({(p_ref, alpha_ref)} | {(p, a) for p in p_candidates if p <= h.N for a in alpha_candidates})
+    for p, a in cands:
+        with fwbf.Code.from_parity_check(h, p) as code:
+            bits, iters = code.outputs(frames)
+            ms = _time(lambda: fwbf.fwbf_decode(code.handle, q, max_iter, a, bits, iters))
+            fe = _frame_errors(bits, iters, c)
+        r = {"p": p, "alpha": a, "frame_errors": fe, "ms": ms}
+        results.append(r)
+        if (p, a) == (p_ref, alpha_ref):
+            ref = r
+        if log:
+            log(r)
+    qualified = [r for r in results if r["frame_errors"] <= ref["frame_errors"]]
+    best = min(qualified, key=lambda r: r["ms"])
+    return {"choice": {"p": best["p"], "alpha": best["alpha"]}, "reference": ref, "candidates": results,
+            "frames": frames, "ebn0_db": ebn0}
+
+
+def tune_batch_shape(jobs, warps_candidates=(4, 8, 12, 16), packed_candidates=(1, 0)):
+    """Fastest (warps_per_cta, packed) for a batch of jobs [(code, y, max_iter,
+    alpha, bits, iters)]; both variants give identical results."""
+    best = None
+    rows = []
+    for packed in packed_candidates:
+        for w in warps_candidates:
+            b = fwbf.fwbf_batch_create(jobs, warps_per_cta=w, packed=packed)
+            try:
+                ms = _time(lambda: fwbf.fwbf_decode_batch(b))
+            finally:
+                fwbf.fwbf_batch_destroy(b)
+            rows.append({"warps_per_cta": w, "packed": packed, "ms": ms})
+            if best is None or ms < best["ms"]:
+                best = rows[-1]
+    return best, rows
+
+
+class Cache:
+    def __init__(self, path: str = DEFAULT_CACHE):
+        self.path = path
+        try:
+            with open(path) as f:
+                self.data = json.load(f)
+        except (OSError, ValueError):
+            self.data = {}
+
+    def key(self, h, ebn0, what="code"):
+        import torch
+
+        return f"{what}:{code_key(h)}:{ebn0:.3f}:{torch.cuda.get_device_name()}"
+
+    def get(self, k):
+        return self.data.get(k)
+
+    def put(self, k, v):
+        self.data[k] = v
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
+        tmp = self.path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(self.data, f, indent=1)
+        os.replace(tmp, self.path)
+
+
+def tuned_code(h, enc, ebn0, p_ref, alpha_ref=1.5, cache: Cache | None = None, **kw):
+    cache = cache or Cache()
+    k = cache.key(h, ebn0)
+    hit = cache.get(k)
+    if hit is None:
+        t0 = time.time()
+        hit = tune_code(h, enc, ebn0, p_ref, alpha_ref, **kw)
+        hit["tune_seconds"] = time.time() - t0
+        cache.put(k, hit)
+    return hit

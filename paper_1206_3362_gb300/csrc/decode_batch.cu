@@ -1,0 +1,246 @@
+// Batched FWBF decoding: one persistent launch over several codes, each with
+// its own frames and outputs (codes of different N, M and row / column
+// weight in the same launch).
+//
+// The batch handle holds a device table of jobs (one per code) and one frame
+// counter per job.  Every CTA walks the jobs, starting at job
+// blockIdx.x mod n_jobs so that CTAs spread over the codes: for each job with
+// frames left it copies the job descriptor into shared memory, stages that
+// code's index tables with a bulk copy (TMA) on a fresh mbarrier, lays its
+// warps' shared-memory slices out for that code and lets each warp pull frames
+// from the job's counter until the job is exhausted; then the CTA moves on.
+// Per frame a warp runs the packed cyclic decoder (cyclic codes) or the
+// generic list decoder (every other code) -- the same device code as the
+// single-code kernels, so results are identical to fwbf_decode.
+//
+// A decode call is a memset of the counters plus one launch on the caller's
+// stream; it allocates nothing, so it can be captured in a CUDA graph.
+#include <math.h>
+
+#include <vector>
+
+#include "cyclic_frame.cuh"
+#include "generic_frame.cuh"
+
+namespace fwbf {
+
+__device__ int g_status_batch;
+
+enum JobKind : int { kJobGenericPlain = 0, kJobGenericCirc = 1, kJobCyclic4 = 2, kJobCyclic8 = 3, kJobCyclic2 = 4,
+                     kJobCyclic1 = 5 };
+
+struct BatchJob {
+    int kind;
+    int warps;  // warps of a CTA that decode this job (shared memory permitting)
+    uint32_t table_smem_bytes;
+    uint32_t warp_bytes;
+    unsigned long long *counter;
+    long long F;
+    I8Params gp;
+    CyclicParams cp;
+};
+
+constexpr int kMaxJobs = 16;
+
+__global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJob *__restrict__ jobs, int n_jobs) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint64_t bars[kMaxJobs];
+    __shared__ int flag;
+    __shared__ BatchJob J;
+    __shared__ uint32_t d_off[128], u_off[128];
+    __shared__ int live;
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    for (int t = 0; t < n_jobs; ++t) {
+        const int j = (blockIdx.x + t) % n_jobs;
+        if (threadIdx.x == 0) {
+            J = jobs[j];
+            live = atomicAdd(J.counter, 0ull) < (unsigned long long)J.F;
+        }
+        __syncthreads();
+        if (!live) {
+            __syncthreads();
+            continue;
+        }
+        const uint32_t words = J.kind <= kJobGenericCirc ? J.gp.table_words : J.cp.table_words;
+        const uint32_t *gtab = J.kind <= kJobGenericCirc ? J.gp.table : J.cp.table;
+        uint32_t *st = reinterpret_cast<uint32_t *>(smem);
+        if (!stage_table(st, gtab, words, &bars[t], &flag)) {
+            if (threadIdx.x == 0) atomicOr(&g_status_batch, 1);
+            return;
+        }
+        if (J.kind >= kJobCyclic4) {
+            for (int e = threadIdx.x; e < J.cp.DC; e += blockDim.x) {
+                d_off[e] = st[J.cp.rent_off + e] & 0xffffu;
+                u_off[e] = st[J.cp.cent_off + e] & 0xffffu;
+            }
+        }
+        __syncthreads();
+        if (warp < J.warps) {
+            unsigned char *ws = smem + J.table_smem_bytes + warp * J.warp_bytes;
+            const int B = J.kind <= kJobGenericCirc ? J.gp.B : J.cp.B;
+            const uint32_t off_keys = J.kind <= kJobGenericCirc ? J.gp.off_keys : J.cp.off_keys;
+            unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + off_keys);
+            for (int b = lane; b < B; b += 32) keys[b] = 0ull;
+            __syncwarp();
+            for (;;) {
+                unsigned long long f = 0;
+                if (lane == 0) f = atomicAdd(J.counter, 1ull);
+                f = __shfl_sync(FULL, f, 0);
+                if (f >= (unsigned long long)J.F) break;
+                switch (J.kind) {
+                    case kJobGenericPlain: generic_frame<true>(J.gp, st, ws, lane, f); break;
+                    case kJobGenericCirc: generic_frame<false>(J.gp, st, ws, lane, f); break;
+                    case kJobCyclic8: cyclic_frame<8>(J.cp, d_off, u_off, ws, lane, f); break;
+                    case kJobCyclic4: cyclic_frame<4>(J.cp, d_off, u_off, ws, lane, f); break;
+                    case kJobCyclic2: cyclic_frame<2>(J.cp, d_off, u_off, ws, lane, f); break;
+                    default: cyclic_frame<1>(J.cp, d_off, u_off, ws, lane, f); break;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace fwbf
+
+using namespace fwbf;
+
+struct fwbf_batch_s {
+    int n_jobs = 0;
+    BatchJob *d_jobs = nullptr;
+    unsigned long long *d_counters = nullptr;
+    int blocks = 0, threads = 0;
+    uint32_t dyn = 0;
+    int device = 0;
+};
+
+extern "C" {
+
+int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_per_cta, int32_t packed,
+                      fwbf_batch *out) {
+    if (!out) return fail(FWBF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs) return fail(FWBF_EINVAL, "n_jobs must be in [1, 16]");
+    if (warps_per_cta < 1 || warps_per_cta > 16) return fail(FWBF_EINVAL, "warps_per_cta must be in [1, 16]");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::vector<BatchJob> hj((size_t)n_jobs);
+    int optin = 0, sms = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    const uint32_t reserve = 4096u;  // static shared memory of the kernel
+    uint32_t dyn = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const fwbf_batch_job &in = jobs[j];
+        const fwbf_code_s *c = in.code;
+        if (!c) return fail(FWBF_EINVAL, "job code is NULL");
+        if (c->device != dev) return fail(FWBF_EINVAL, "job code was created on another device");
+        if (in.n_frames < 0 || in.max_iter < 1 || !(in.alpha >= 0.0f && in.alpha <= 64.0f))
+            return fail(FWBF_EINVAL, "bad job frames / max_iter / alpha");
+        if (in.n_frames > 0 && (!in.y || !in.out_bits || !in.out_iters)) return fail(FWBF_EINVAL, "NULL job buffer");
+        if (reinterpret_cast<uintptr_t>(in.y) % 16) return fail(FWBF_EINVAL, "job y must be 16-byte aligned");
+        BatchJob &b = hj[j];
+        b = BatchJob{};
+        const int aq = (int)nearbyint((double)in.alpha * 256.0);
+        if (packed && cyclic_eligible(c)) {
+            cyclic_layout(c, b.cp);
+            const int R = cyclic_R(c);
+            b.kind = R == 8 ? kJobCyclic8 : R == 4 ? kJobCyclic4 : R == 2 ? kJobCyclic2 : kJobCyclic1;
+            b.cp.y = in.y;
+            b.cp.F = in.n_frames;
+            b.cp.max_iter = in.max_iter;
+            b.cp.alpha_q = aq;
+            b.cp.out_bits = in.out_bits;
+            b.cp.out_iters = in.out_iters;
+            b.table_smem_bytes = b.cp.table_smem_bytes;
+            b.warp_bytes = b.cp.warp_bytes;
+        } else {
+            generic_layout(c, b.gp);
+            b.kind = c->Z == 1 ? kJobGenericPlain : kJobGenericCirc;
+            b.gp.y = in.y;
+            b.gp.F = in.n_frames;
+            b.gp.max_iter = in.max_iter;
+            b.gp.alpha_q = aq;
+            b.gp.out_bits = in.out_bits;
+            b.gp.out_iters = in.out_iters;
+            b.table_smem_bytes = (c->table_words * 4u + 15u) & ~15u;
+            b.gp.table_in_smem = 1;
+            b.gp.table_smem_bytes = b.table_smem_bytes;
+            b.warp_bytes = b.gp.warp_bytes;
+        }
+        b.F = in.n_frames;
+        if (b.table_smem_bytes + b.warp_bytes + reserve > (uint32_t)optin)
+            return fail(FWBF_EUNSUPPORTED, "a job's code does not fit one warp's shared memory");
+        b.warps = (int)(((uint32_t)optin - reserve - b.table_smem_bytes) / b.warp_bytes);
+        if (b.warps > warps_per_cta) b.warps = warps_per_cta;
+        const uint32_t need = b.table_smem_bytes + b.warps * b.warp_bytes;
+        if (need > dyn) dyn = need;
+    }
+    fwbf_batch_s *bh = new (std::nothrow) fwbf_batch_s();
+    if (!bh) return fail(FWBF_ENOMEM, "host allocation");
+    bh->n_jobs = n_jobs;
+    bh->device = dev;
+    bh->threads = 32 * warps_per_cta;
+    bh->dyn = dyn;
+    e = cudaMalloc(reinterpret_cast<void **>(&bh->d_counters), sizeof(unsigned long long) * n_jobs);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&bh->d_jobs), sizeof(BatchJob) * n_jobs);
+    if (e != cudaSuccess) {
+        cudaFree(bh->d_counters);
+        delete bh;
+        return e == cudaErrorMemoryAllocation ? fail(FWBF_ENOMEM, "cudaMalloc(batch)") : cuda_fail(e, "cudaMalloc");
+    }
+    for (int j = 0; j < n_jobs; ++j) {
+        hj[j].counter = bh->d_counters + j;
+        hj[j].gp.counter = hj[j].counter;
+        hj[j].cp.counter = hj[j].counter;
+    }
+    e = cudaMemcpy(bh->d_jobs, hj.data(), sizeof(BatchJob) * n_jobs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fwbf_decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwbf_decode_batch_kernel, bh->threads, dyn);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaFree(bh->d_counters);
+        cudaFree(bh->d_jobs);
+        delete bh;
+        return e != cudaSuccess ? cuda_fail(e, "batch set-up") : fail(FWBF_EUNSUPPORTED, "batch kernel does not fit");
+    }
+    bh->blocks = per_sm * sms;
+    *out = bh;
+    return FWBF_OK;
+}
+
+int fwbf_decode_batch(fwbf_batch b, void *stream) {
+    if (!b) return fail(FWBF_EINVAL, "batch is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * b->n_jobs, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counters)");
+    fwbf_decode_batch_kernel<<<b->blocks, b->threads, b->dyn, s>>>(b->d_jobs, b->n_jobs);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "decode_batch launch");
+}
+
+int fwbf_batch_destroy(fwbf_batch b) {
+    if (!b) return FWBF_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(b->d_counters);
+    cudaFree(b->d_jobs);
+    delete b;
+    return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "cudaDeviceSynchronize");
+}
+
+int fwbf_batch_status(void *stream) {
+    int v = 0, zero = 0;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, g_status_batch, sizeof(int));
+    if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_status_batch, &zero, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "batch status");
+    return v ? fail(FWBF_ETIMEOUT, "the batch kernel gave up waiting for a table copy") : FWBF_OK;
+}
+
+}  // extern "C"

@@ -30,6 +30,12 @@ class FwbfError(RuntimeError):
         self.status = status
 
 
+class BatchJob(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
+                ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("out_bits", ctypes.c_void_p),
+                ("out_iters", ctypes.c_void_p)]
+
+
 class CodeInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("Z", ctypes.c_int32), ("dv_max", ctypes.c_int32), ("dc_max", ctypes.c_int32),
@@ -64,6 +70,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_mlp_forward": ([P, P, i64, P, P], ctypes.c_int),
         "fwbf_mlp_grad": ([P, P, P, i64, i64, P, P, P], ctypes.c_int),
         "fwbf_mlp_adam": ([P, P, P, P, P, i64, f32, f32, f32, f32, P], ctypes.c_int),
+        "fwbf_batch_create": ([P, i32, i32, i32, ctypes.POINTER(P)], ctypes.c_int),
+        "fwbf_decode_batch": ([P, P], ctypes.c_int),
+        "fwbf_batch_status": ([P], ctypes.c_int),
+        "fwbf_batch_destroy": ([P], ctypes.c_int),
         "fwbf_last_status": ([P], ctypes.c_int),
         "fwbf_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "fwbf_last_error": ([], ctypes.c_char_p),
@@ -261,6 +271,37 @@ def fwbf_mlp_adam(master, blob, grad, m, v, step: int, lr: float, beta1=0.9, bet
                                         _dev(grad, torch.float32, "grad"), _dev(m, torch.float32, "m"),
                                         _dev(v, torch.float32, "v"), int(step), float(lr), float(beta1),
                                         float(beta2), float(eps), _stream(stream)))
+
+
+def fwbf_batch_create(jobs, warps_per_cta: int = 16, packed: int = 1) -> ctypes.c_void_p:
+    """jobs: list of (code handle, y int8 [F][N], max_iter, alpha, out_bits, out_iters)."""
+    import torch
+
+    arr = (BatchJob * len(jobs))()
+    for i, (code, y, max_iter, alpha, bits, iters) in enumerate(jobs):
+        arr[i].code = code.value if isinstance(code, ctypes.c_void_p) else code
+        arr[i].y = _dev(y, torch.int8, "y").value
+        arr[i].n_frames = y.shape[0]
+        arr[i].max_iter = int(max_iter)
+        arr[i].alpha = float(alpha)
+        arr[i].out_bits = _dev(bits, torch.int32, "out_bits").value
+        arr[i].out_iters = _dev(iters, torch.int32, "out_iters").value
+    h = ctypes.c_void_p()
+    _check(load_library().fwbf_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(jobs), int(warps_per_cta),
+                                            int(packed), ctypes.byref(h)))
+    return h
+
+
+def fwbf_decode_batch(batch, stream=None) -> None:
+    _check(load_library().fwbf_decode_batch(batch, _stream(stream)))
+
+
+def fwbf_batch_status(stream=None) -> int:
+    return load_library().fwbf_batch_status(_stream(stream))
+
+
+def fwbf_batch_destroy(batch) -> None:
+    _check(load_library().fwbf_batch_destroy(batch))
 
 
 def fwbf_last_status(stream=None) -> int:
