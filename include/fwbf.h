@@ -166,6 +166,9 @@ typedef struct {
     float alpha;           /* 0 <= alpha <= 64 */
     uint32_t *out_bits;    /* device uint32 [n_frames][ceil(N/32)] */
     int32_t *out_iters;    /* device int32 [n_frames] */
+    const void *mlp;       /* NULL: plain FWBF; else the learned network (see
+                              fwbf_decode_learned), cyclic codes with packed = 1 only */
+    int32_t k_learn;       /* learned passes before the plain fallback (mlp != NULL) */
 } fwbf_batch_job;
 
 /*

@@ -106,6 +106,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     const uint32_t my_u = lane < DC ? u_off[lane] : 0u;  // column offset of row position e = lane
     const int bias = 128 * DC + 0x4000;
     const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
+    const float inv_Z = 1.0f / (float)Z, inv_B = 1.0f / (float)P.B;
 
     // ---- frame load (aligned 16-byte chunks; byte loads at the buffer end)
     const uintptr_t fb = ybase + (uintptr_t)(f * (unsigned long long)Z);
@@ -237,12 +238,12 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         int aq = P.alpha_q, tq = P.theta_q;
         if (mode != kModePlain || P.out_feat) {
             float feat[kFeatures];
-            feat[0] = (float)W / (float)Z;
-            feat[1] = (float)Wprev / (float)Z;
-            feat[2] = (float)W0 / (float)Z;
+            feat[0] = (float)W * inv_Z;
+            feat[1] = (float)Wprev * inv_Z;
+            feat[2] = (float)W0 * inv_Z;
             feat[3] = (float)k * (1.0f / 16.0f);
-            feat[4] = (float)nflip_prev / (float)P.B;
-            feat[5] = (float)ncand_prev / (float)Z;
+            feat[4] = (float)nflip_prev * inv_B;
+            feat[5] = (float)ncand_prev * inv_Z;
             feat[6] = mean_a;
             feat[7] = weak_frac;
             const int kk = passes_before + k;

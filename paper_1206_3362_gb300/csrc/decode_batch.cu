@@ -143,6 +143,10 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
             return fail(FWBF_EINVAL, "bad job frames / max_iter / alpha");
         if (in.n_frames > 0 && (!in.y || !in.out_bits || !in.out_iters)) return fail(FWBF_EINVAL, "NULL job buffer");
         if (reinterpret_cast<uintptr_t>(in.y) % 16) return fail(FWBF_EINVAL, "job y must be 16-byte aligned");
+        if (in.mlp && (!packed || !cyclic_eligible(c)))
+            return fail(FWBF_EUNSUPPORTED, "a learned job needs a cyclic code and the packed decoder");
+        if (in.mlp && (in.k_learn < 1 || reinterpret_cast<uintptr_t>(in.mlp) % 16))
+            return fail(FWBF_EINVAL, "learned job: k_learn < 1 or unaligned network blob");
         BatchJob &b = hj[j];
         b = BatchJob{};
         const int aq = (int)nearbyint((double)in.alpha * 256.0);
@@ -156,6 +160,11 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
             b.cp.alpha_q = aq;
             b.cp.out_bits = in.out_bits;
             b.cp.out_iters = in.out_iters;
+            if (in.mlp) {
+                b.cp.mode = 2;
+                b.cp.mlp = static_cast<const unsigned char *>(in.mlp);
+                b.cp.k_learn = in.k_learn;
+            }
             b.table_smem_bytes = b.cp.table_smem_bytes;
             b.warp_bytes = b.cp.warp_bytes;
         } else {

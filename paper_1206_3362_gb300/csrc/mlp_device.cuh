@@ -27,45 +27,63 @@ constexpr int kPW1 = 0, kPW2 = 512, kPW3 = 4608, kPB1 = 4736, kPB2 = 4800, kPB3 
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-// out0, out1 = network(feat) for the whole warp (feat identical in every lane)
+// out0, out1 = network(feat) for the whole warp (feat identical in every lane).
+// Lane l computes hidden units l and l + 32 of both layers; the second layer
+// reads its 64 inputs by shuffles, its weight rows as 128-bit loads (8 bf16),
+// and keeps four partial sums per unit so the FMA chains are short.
 __device__ __forceinline__ void mlp_eval(const unsigned char *blob, const float *feat, int lane, float &out0,
                                          float &out1) {
     const uint32_t *W1 = reinterpret_cast<const uint32_t *>(blob + kMlpW1);
-    const uint32_t *W2 = reinterpret_cast<const uint32_t *>(blob + kMlpW2);
+    const uint4 *W2 = reinterpret_cast<const uint4 *>(blob + kMlpW2);  // 8 uint4 per row
     const uint32_t *W3 = reinterpret_cast<const uint32_t *>(blob + kMlpW3);
     const float *b1 = reinterpret_cast<const float *>(blob + kMlpB1);
     const float *b2 = reinterpret_cast<const float *>(blob + kMlpB2);
     const float *b3 = reinterpret_cast<const float *>(blob + kMlpB3);
+    const uint4 w1a = __ldg(reinterpret_cast<const uint4 *>(W1) + lane);
+    const uint4 w1b = __ldg(reinterpret_cast<const uint4 *>(W1) + lane + 32);
     float ha = __ldg(b1 + lane), hb = __ldg(b1 + lane + 32);
+    float ta = bf16_lo(w1a.x) * feat[0], tb = bf16_lo(w1b.x) * feat[0];
+    ha = fmaf(bf16_hi(w1a.x), feat[1], ha);
+    hb = fmaf(bf16_hi(w1b.x), feat[1], hb);
+    ta = fmaf(bf16_lo(w1a.y), feat[2], ta);
+    tb = fmaf(bf16_lo(w1b.y), feat[2], tb);
+    ha = fmaf(bf16_hi(w1a.y), feat[3], ha);
+    hb = fmaf(bf16_hi(w1b.y), feat[3], hb);
+    ta = fmaf(bf16_lo(w1a.z), feat[4], ta);
+    tb = fmaf(bf16_lo(w1b.z), feat[4], tb);
+    ha = fmaf(bf16_hi(w1a.z), feat[5], ha);
+    hb = fmaf(bf16_hi(w1b.z), feat[5], hb);
+    ta = fmaf(bf16_lo(w1a.w), feat[6], ta);
+    tb = fmaf(bf16_lo(w1b.w), feat[6], tb);
+    ha = fmaf(bf16_hi(w1a.w), feat[7], ha);
+    hb = fmaf(bf16_hi(w1b.w), feat[7], hb);
+    ha = fmaxf(ha + ta, 0.0f);
+    hb = fmaxf(hb + tb, 0.0f);
+    float ga[4] = {__ldg(b2 + lane), 0.0f, 0.0f, 0.0f};
+    float gb[4] = {__ldg(b2 + lane + 32), 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        const uint32_t wa = __ldg(W1 + lane * 4 + w), wb = __ldg(W1 + (lane + 32) * 4 + w);
-        ha = fmaf(bf16_lo(wa), feat[2 * w], ha);
-        ha = fmaf(bf16_hi(wa), feat[2 * w + 1], ha);
-        hb = fmaf(bf16_lo(wb), feat[2 * w], hb);
-        hb = fmaf(bf16_hi(wb), feat[2 * w + 1], hb);
+    for (int v = 0; v < 8; ++v) {  // inputs 8v .. 8v + 7
+        const uint4 wa = __ldg(W2 + lane * 8 + v), wb = __ldg(W2 + (lane + 32) * 8 + v);
+        const float src = v < 4 ? ha : hb;
+        float x[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = __shfl_sync(0xffffffffu, src, (8 * v + t) & 31);
+        const uint32_t aw[4] = {wa.x, wa.y, wa.z, wa.w}, bw[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            ga[t] = fmaf(bf16_lo(aw[t]), x[2 * t], ga[t]);
+            ga[t] = fmaf(bf16_hi(aw[t]), x[2 * t + 1], ga[t]);
+            gb[t] = fmaf(bf16_lo(bw[t]), x[2 * t], gb[t]);
+            gb[t] = fmaf(bf16_hi(bw[t]), x[2 * t + 1], gb[t]);
+        }
     }
-    ha = fmaxf(ha, 0.0f);
-    hb = fmaxf(hb, 0.0f);
-    float ga = __ldg(b2 + lane), gb = __ldg(b2 + lane + 32);
-#pragma unroll 4
-    for (int w = 0; w < 32; ++w) {  // inputs 2w, 2w + 1
-        const float src = w < 16 ? ha : hb;
-        const int l0 = (2 * w) & 31;
-        const float x0 = __shfl_sync(0xffffffffu, src, l0), x1 = __shfl_sync(0xffffffffu, src, l0 + 1);
-        const uint32_t wa = __ldg(W2 + lane * 32 + w), wb = __ldg(W2 + (lane + 32) * 32 + w);
-        ga = fmaf(bf16_lo(wa), x0, ga);
-        ga = fmaf(bf16_hi(wa), x1, ga);
-        gb = fmaf(bf16_lo(wb), x0, gb);
-        gb = fmaf(bf16_hi(wb), x1, gb);
-    }
-    ga = fmaxf(ga, 0.0f);
-    gb = fmaxf(gb, 0.0f);
+    const float g1 = fmaxf((ga[0] + ga[1]) + (ga[2] + ga[3]), 0.0f);
+    const float g2 = fmaxf((gb[0] + gb[1]) + (gb[2] + gb[3]), 0.0f);
     const uint32_t r0a = __ldg(W3 + (lane >> 1)), r0b = __ldg(W3 + 16 + (lane >> 1));
     const uint32_t r1a = __ldg(W3 + 32 + (lane >> 1)), r1b = __ldg(W3 + 48 + (lane >> 1));
     const bool odd = lane & 1;
-    float p0 = (odd ? bf16_hi(r0a) : bf16_lo(r0a)) * ga + (odd ? bf16_hi(r0b) : bf16_lo(r0b)) * gb;
-    float p1 = (odd ? bf16_hi(r1a) : bf16_lo(r1a)) * ga + (odd ? bf16_hi(r1b) : bf16_lo(r1b)) * gb;
+    float p0 = (odd ? bf16_hi(r0a) : bf16_lo(r0a)) * g1 + (odd ? bf16_hi(r0b) : bf16_lo(r0b)) * g2;
+    float p1 = (odd ? bf16_hi(r1a) : bf16_lo(r1a)) * g1 + (odd ? bf16_hi(r1b) : bf16_lo(r1b)) * g2;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         p0 += __shfl_xor_sync(0xffffffffu, p0, d);

@@ -33,7 +33,7 @@ class FwbfError(RuntimeError):
 class BatchJob(ctypes.Structure):
     _fields_ = [("code", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
                 ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("out_bits", ctypes.c_void_p),
-                ("out_iters", ctypes.c_void_p)]
+                ("out_iters", ctypes.c_void_p), ("mlp", ctypes.c_void_p), ("k_learn", ctypes.c_int32)]
 
 
 class CodeInfo(ctypes.Structure):
@@ -274,11 +274,16 @@ def fwbf_mlp_adam(master, blob, grad, m, v, step: int, lr: float, beta1=0.9, bet
 
 
 def fwbf_batch_create(jobs, warps_per_cta: int = 16, packed: int = 1) -> ctypes.c_void_p:
-    """jobs: list of (code handle, y int8 [F][N], max_iter, alpha, out_bits, out_iters)."""
+    """jobs: list of (code handle, y int8 [F][N], max_iter, alpha, out_bits,
+    out_iters[, mlp blob uint8 tensor, k_learn])."""
     import torch
 
     arr = (BatchJob * len(jobs))()
-    for i, (code, y, max_iter, alpha, bits, iters) in enumerate(jobs):
+    for i, job in enumerate(jobs):
+        code, y, max_iter, alpha, bits, iters = job[:6]
+        if len(job) > 6 and job[6] is not None:
+            arr[i].mlp = _dev(job[6], torch.uint8, "mlp").value
+            arr[i].k_learn = int(job[7])
         arr[i].code = code.value if isinstance(code, ctypes.c_void_p) else code
         arr[i].y = _dev(y, torch.int8, "y").value
         arr[i].n_frames = y.shape[0]

@@ -280,34 +280,101 @@ def train_pipeline(code, enc, train_frames: int, ebn0_list, sch: Schedule, epoch
                  "losses": losses, "train_seconds": time.time() - t0}
 
 
+def evaluate_batched(code, q, c, net: Network | None, sch: Schedule, max_iter: int = 100, reps: int = 3,
+                     warps_per_cta: int = 16):
+    """As evaluate(), through one graph-captured batched launch (the learned
+    network, if given, runs inside the batch kernel)."""
+    import torch
+
+    F = q.shape[0]
+    bits, iters = code.outputs(F, q.device)
+    job = (code.handle, q, max_iter, sch.alpha_default, bits, iters)
+    if net is not None:
+        job = job + (net.blob, sch.k_learn)
+    batch = fwbf.fwbf_batch_create([job], warps_per_cta=warps_per_cta, packed=1)
+    s = torch.cuda.Stream()
+    try:
+        with torch.cuda.stream(s):
+            fwbf.fwbf_decode_batch(batch, s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fwbf.fwbf_decode_batch(batch, s)
+        # replay() launches on the current stream: time it there
+        with torch.cuda.stream(s):
+            g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                g.replay()
+            e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    finally:
+        fwbf.fwbf_batch_destroy(batch)
+    ok = frame_ok(bits, iters, c)
+    fe = int((~ok).sum().item())
+    be = int((unpack_bits_torch(bits, c.shape[1]) != c).sum().item())
+    passes = torch.where(iters >= 0, iters, torch.full_like(iters, max_iter)).float().mean().item()
+    return {"frames": F, "frame_errors": fe, "fer": fe / F, "fer_ci95": wilson(fe, F),
+            "ber": be / (F * c.shape[1]), "avg_passes": passes, "decode_ms": ms}
+
+
 def main():
+    """Config: EG(1023,781), 3.0-4.5 dB; autotune (p, alpha) at 4 dB, label and
+    train on seeded frames, evaluate plain (paper setting), tuned plain and
+    learned (batched, graph-captured) on held-out frames."""
     import argparse
     import json
 
     import torch
 
+    from . import autotune
     from .inputs import Encoder, make_code
 
-    ap = argparse.ArgumentParser(description="train the learned FWBF schedule on EG(1023,781)")
-    ap.add_argument("--train-frames", type=int, default=1 << 20)
-    ap.add_argument("--eval-frames", type=int, default=1 << 18)
-    ap.add_argument("--seg-len", type=int, default=8)
+    ap = argparse.ArgumentParser(description="train and evaluate the learned FWBF schedule on EG(1023,781)")
+    ap.add_argument("--train-frames", type=int, default=1 << 22)
+    ap.add_argument("--eval-frames", type=int, default=1 << 18, help="held-out frames per Eb/N0 point")
     ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--k-learn", type=int, default=8)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--report", default=None)
+    ap.add_argument("--weights", default=None, help="evaluate these weights instead of training")
     args = ap.parse_args()
     torch.cuda.set_device(0)
     h = make_code("eg1023")
     enc = Encoder(h)
-    sch = Schedule()
     ebn0 = (3.0, 3.5, 4.0, 4.5)
-    code = fwbf.Code.from_parity_check(h, args.seg_len)
-    net, summary = train_pipeline(code, enc, args.train_frames, ebn0, sch, epochs=args.epochs)
-    net.save(args.out, seg_len=args.seg_len, k_learn=sch.k_learn, alpha_default=sch.alpha_default)
-    res = {"train": summary}
+    tune = autotune.tune_code(h, enc, 4.0, p_ref=31, alpha_ref=1.5, frames=1 << 16)
+    p_star, a_star = tune["choice"]["p"], tune["choice"]["alpha"]
+    print(json.dumps({"autotune": tune["choice"], "reference": tune["reference"]}), flush=True)
+    sch = Schedule(alpha_default=a_star, k_learn=args.k_learn)
+    code = fwbf.Code.from_parity_check(h, p_star)
+    if args.weights:
+        net = Network(alpha_default=sch.alpha_default)
+        meta = net.load(args.weights)
+        summary = {"weights": os.path.basename(args.weights), "seg_len": int(meta["seg_len"])}
+        if int(meta["seg_len"]) != p_star or float(meta["alpha_default"]) != a_star:
+            p_star, a_star = int(meta["seg_len"]), float(meta["alpha_default"])
+            sch = Schedule(alpha_default=a_star, k_learn=int(meta["k_learn"]))
+            code = fwbf.Code.from_parity_check(h, p_star)
+    else:
+        net, summary = train_pipeline(code, enc, args.train_frames, ebn0, sch, epochs=args.epochs,
+                                      log=lambda m: print(m, flush=True))
+        net.save(args.out, seg_len=p_star, k_learn=sch.k_learn, alpha_default=sch.alpha_default)
+    res = {"autotune": tune, "train": summary, "seg_len": p_star, "alpha": a_star, "k_learn": sch.k_learn}
+    paper = Schedule(alpha_default=1.5, k_learn=sch.k_learn)
+    code31 = fwbf.Code.from_parity_check(h, 31)
     for eb in ebn0:
         q, c = make_frames(code, enc, args.eval_frames, (eb,), seed=777, device="cuda")
-        res[f"{eb}dB"] = {"plain": evaluate(code, q, c, None, sch), "learned": evaluate(code, q, c, net, sch)}
-    print(json.dumps(res))
+        res[f"{eb}dB"] = {"plain_p31": evaluate(code31, q, c, None, paper),
+                          "plain_tuned": evaluate(code, q, c, None, sch),
+                          "learned_batched": evaluate_batched(code, q, c, net, sch)}
+        print(json.dumps({f"{eb}dB": res[f"{eb}dB"]}), flush=True)
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(res, f, indent=1)
 
 
 if __name__ == "__main__":
