@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--frames", type=int, default=WORKLOAD["frames"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="eg1023", choices=["eg1023", "batched4"],
+                    help="eg1023: EG(1023,781) at 4 dB (default); batched4: four codes in one graph-captured launch")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the autotuned and learned batched forms on the same frames")
     return ap.parse_args()
 
 
@@ -160,6 +164,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload == "batched4":
+        run_batched4(args)
+        return
 
     import numpy as np
     import torch
@@ -262,6 +269,8 @@ def main():
         "clocks": clock_info,
     }
 
+    if rank == 0 and not args.no_compare:
+        result["comparison"] = compare_forms(fwbf, h, enc, q, c, w, F, fer, value, dev)
     if rank == 0 and not args.no_e2e:
         result["e2e"] = e2e(args, fwbf, code, y, w, F, enc, dev, stream)
     if rank == 0 and not args.no_cpu:
@@ -271,6 +280,111 @@ def main():
     code.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+BATCH_MIX = [("rand504", 32, 4), ("rand2016", 32, 2), ("eg4095", 63, 1), ("qc8192", 64, 1)]
+
+
+def run_batched4(args):
+    """Four codes of uneven N, M and weights (random (3,6) N=504 and N=2016,
+    EG(4095,3367), QC N=8192 Z=256), frames 4:2:1:1 summing to 2^20 at 4 dB,
+    decoded by one persistent launch captured in a CUDA graph; p, alpha,
+    warps per CTA and packing from the autotuner."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1206_3362_gb300 import autotune, fwbf, learned
+    from paper_1206_3362_gb300.inputs import Encoder, make_code
+    from paper_1206_3362_gb300.inputs.channel import bpsk_awgn_torch, random_codewords_torch
+
+    torch.cuda.set_device(0)
+    total = args.frames
+    jobs, keep, info_bits, tunes = [], [], 0, {}
+    for i, (key, p_ref, share) in enumerate(BATCH_MIX):
+        h = make_code(key)
+        enc = Encoder(h)
+        F = total * share // 8
+        t = autotune.tune_code(h, enc, 4.0, p_ref=p_ref, alpha_ref=1.5, frames=1 << 14,
+                               p_candidates=(4, 8, 16, 32, 64), alpha_candidates=(1.5, 2.0))
+        p, a = t["choice"]["p"], t["choice"]["alpha"]
+        tunes[key] = {"p": p, "alpha": a, "frames": F, "N": h.N, "K": enc.K}
+        _, c = random_codewords_torch(enc, F, seed=300 + i, device="cuda")
+        q = fwbf.quantize(bpsk_awgn_torch(c, 4.0, enc.rate, seed=300 + i).contiguous())
+        code = fwbf.Code.from_parity_check(h, p)
+        bits, iters = code.outputs(F)
+        jobs.append((code.handle, q, 100, a, bits, iters))
+        keep.append((code, q, c, bits, iters, enc))
+        info_bits += F * enc.K
+    shape, rows = autotune.tune_batch_shape(jobs)
+    batch = fwbf.fwbf_batch_create(jobs, warps_per_cta=shape["warps_per_cta"], packed=shape["packed"])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        fwbf.fwbf_decode_batch(batch, s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fwbf.fwbf_decode_batch(batch, s)
+    with torch.cuda.stream(s):
+        for _ in range(max(3, args.warmup)):
+            g.replay()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    assert fwbf.fwbf_batch_status() == 0
+    for (code, q, c, bits, iters, enc), key in zip(keep, tunes):
+        tunes[key]["fer"] = float((~learned.frame_ok(bits, iters, c)).float().mean().item())
+    fwbf.fwbf_batch_destroy(batch)
+    print(json.dumps({
+        "metric": METRIC, "value": info_bits / (ms / 1e3) / 1e9, "unit": "Gb/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": "batched: rand(3,6) N=504 / N=2016, EG(4095,3367), QC N=8192 Z=256; frames "
+                               "4:2:1:1 of %d at Eb/N0 4 dB, one graph-captured persistent launch" % total,
+                   "codes": tunes, "batch_shape": shape, "l2": "inputs larger than L2 (no flush)"},
+        "gpu_launches": args.steps, "clocks": clock_info}))
+
+
+def compare_forms(fwbf, h, enc, q, c, w, F, fer_plain, gbps_plain, dev):
+    """The same frames through the throughput forms: the autotuned plain
+    decoder (FER-qualified p and alpha) and the learned schedule, each as one
+    graph-captured batched launch.  Decoded info Gb/s here covers the decode
+    only (the quantised frames are reused)."""
+    import torch
+
+    from paper_1206_3362_gb300 import autotune, learned
+
+    out = {"plain_paper_setting": {"p": w["seg_len"], "alpha": w["alpha"], "fer": fer_plain,
+                                   "gbps_with_quantise": gbps_plain}}
+    tune = autotune.tune_code(h, enc, w["ebn0_db"], p_ref=w["seg_len"], alpha_ref=w["alpha"], frames=1 << 15)
+    p_t, a_t = tune["choice"]["p"], tune["choice"]["alpha"]
+    forms = [("plain_paper_setting", w["seg_len"], w["alpha"], None),
+             ("tuned_batched", p_t, a_t, None)]
+    if os.path.exists(learned.DEFAULT_WEIGHTS):
+        net = learned.Network(alpha_default=a_t)
+        meta = net.load(learned.DEFAULT_WEIGHTS)
+        forms.append(("learned_batched", int(meta["seg_len"]), float(meta["alpha_default"]), net))
+    for name, p, a, net in forms:
+        code = fwbf.Code.from_parity_check(h, p)
+        sch = learned.Schedule(alpha_default=a, k_learn=8)
+        r = learned.evaluate_batched(code, q, c, net, sch, max_iter=w["max_iter"], reps=3)
+        code.close()
+        entry = out.setdefault(name, {})
+        entry.update({"p": p, "alpha": a, "fer": r["fer"], "fer_ci95": r["fer_ci95"],
+                      "avg_passes": r["avg_passes"], "decode_ms": r["decode_ms"],
+                      "gbps_decode": F * enc.K / (r["decode_ms"] / 1e3) / 1e9})
+    out["autotune"] = {"choice": tune["choice"], "calibration_frames": tune["frames"],
+                       "reference_frame_errors": tune["reference"]["frame_errors"]}
+    return out
 
 
 def e2e(args, fwbf, code, y, w, F, enc, dev, stream):
