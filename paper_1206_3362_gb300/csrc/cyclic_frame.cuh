@@ -51,7 +51,7 @@ __device__ __forceinline__ uint32_t vmax_u16x2(uint32_t a, uint32_t b) {
 }
 
 // packed check key of one int8 value: |q| << 8 | (q < 0) << 7
-__device__ __forceinline__ uint32_t qkey(int v) { return ((uint32_t)abs(v) << 8) | ((v < 0) ? 0x80u : 0u); }
+__device__ __forceinline__ uint32_t qkey(int v) { return ((uint32_t)abs(v) << 8) | (((uint32_t)v >> 24) & 0x80u); }
 
 // pair slot of position n: (n, lo) for n < H, (n - H, hi) otherwise
 __device__ __forceinline__ void pair_slot(int n, int H, int &idx, int &shift) {
@@ -60,15 +60,15 @@ __device__ __forceinline__ void pair_slot(int n, int H, int &idx, int &shift) {
     shift = hi ? 16 : 0;
 }
 
-// Rebuilds the doubled array X2[j] = v(j mod Z) | v((j + H) mod Z) << 16.
+// Rebuilds the doubled array X2[j] = v(j mod Z) | v((j + H) mod Z) << 16,
+// j < XJ = Z + H - 1, in three index ranges without modulo arithmetic:
+// j < Z - H: (j, j + H); Z - H <= j < Z: (j, j + H - Z); j >= Z: (j - Z, j - Z + H).
 template <typename F>
 __device__ __forceinline__ void build_doubled(uint32_t *X2, int Z, int H, int XJ, int lane, F v) {
-    for (int j = lane; j < XJ; j += 32) {
-        const int n0 = j < Z ? j : j - Z;
-        int n1 = j + H;
-        n1 = n1 >= Z ? n1 - Z : n1;
-        X2[j] = v(n0) | (v(n1) << 16);
-    }
+    const int zh = Z - H;
+    for (int j = lane; j < zh; j += 32) X2[j] = v(j) | (v(j + H) << 16);
+    for (int j = zh + lane; j < Z; j += 32) X2[j] = v(j) | (v(j - zh) << 16);
+    for (int j = Z + lane; j < XJ; j += 32) X2[j] = v(j - Z) | (v(j - zh) << 16);
 }
 
 // Adds delta to every half-word of the doubled array that holds position m
@@ -165,9 +165,10 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
             par[r] = 0u;
         }
         const uint32_t *xb = X2 + lane + 32 * R * c;
-        for (int e = 0; e < DC; ++e) {
+        uint32_t ek = 0u;  // the row position e in both halves
+#pragma unroll 2
+        for (int e = 0; e < DC; ++e, ek += 0x10001u) {
             const uint32_t *p = xb + d_off[e];
-            const uint32_t ek = (uint32_t)e | ((uint32_t)e << 16);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const uint32_t v = p[32 * r];
