@@ -34,6 +34,12 @@ SM_MAX_MHZ = 2070.0
 
 WORKLOAD = dict(code="eg1023", ebn0_db=4.0, frames=1 << 20, max_iter=100, seg_len=31, alpha=1.5)
 
+# DRAM bytes (read + write) per frame of the decode kernel from one ncu capture
+# (fwbf_decode_i8_cyclic_kernel<8>, 131,072 frames of this workload; scaled by
+# frames, since traffic is the frame bytes in and the decisions out); see
+# profiles/fwbf_decode_i8_eg1023_4dB.md.  Set to None when the kernel changes.
+DECODE_TRAFFIC_BYTES_PER_FRAME = 142.585344e6 / 131072
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -262,8 +268,10 @@ def main():
         "config": workload_config(F), "fer": fer, "failed_frames": fail,
         "avg_passes_converged": conv_iters,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "fwbf_decode_i8_kernel", "decode_ms": dec_ms,
+                     "frac": achieved / peak,
+                     "traffic": (DECODE_TRAFFIC_BYTES_PER_FRAME * F if DECODE_TRAFFIC_BYTES_PER_FRAME else None),
+                     "algorithmic_bytes": F * (N + 4 * ((N + 31) // 32) + 4),
+                     "kernel": "fwbf_decode_i8_cyclic_kernel<8>", "decode_ms": dec_ms,
                      "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (derived)"},
         "gpu_launches": 2 * args.steps,
         "clocks": clock_info,
