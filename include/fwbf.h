@@ -130,6 +130,19 @@ int fwbf_decode_noalloc(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
                         float alpha, uint32_t *out_bits, int32_t *out_iters, void *stream);
 
 /*
+ * Comparison rule: lambda-largest selection (MLP-WBF's bit-choose, Sec. III)
+ * with the IMWBF metric of Eq. 1 in place of FWBF's p-blocks.  Every pass
+ * computes E'_n for all bits from the same syndrome, takes the lambda bits with
+ * the largest metrics one after another (largest remaining, lowest index first
+ * among equals) and flips those with E' > 0.  lambda = 1 is single-bit flipping
+ * (FWBF with p = N); lambda >= N flips every positive metric (FWBF with p = 1).
+ * Arguments as fwbf_decode, plus lambda >= 1 (values above N act as N).
+ */
+int fwbf_decode_lambda(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter,
+                       float alpha, int32_t lambda, uint32_t *out_bits, int32_t *out_iters,
+                       void *stream);
+
+/*
  * FWBF on real channel values, metric of Eq. 1 in float32.
  *   y          device float [n_frames][N] (finite values), any 4-byte alignment
  *   other arguments as fwbf_decode.

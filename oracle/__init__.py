@@ -56,6 +56,7 @@ def _load():
             lib.oracle_fwbf_f64.argtypes = [i32, i32, i64, P, P, i32, P, i64, i32, f64, f64,
                                             P, P, P, P]
             lib.oracle_single_flip_i8.argtypes = [i32, i32, i64, P, P, P, i64, i32, i32, i32, P, P]
+            lib.oracle_lambda_i8.argtypes = [i32, i32, i64, P, P, i32, P, i64, i32, i32, i32, P, P]
             _lib = lib
     return _lib
 
@@ -161,6 +162,20 @@ def single_flip_i8(code, q: np.ndarray, max_iter: int, alpha: float = 1.0, theta
     iters = np.zeros(F, dtype=np.int32)
     _check(lib.oracle_single_flip_i8(code.N, code.M, rows.size, _ptr(rows), _ptr(cols), _ptr(q), F,
                                      int(max_iter), alpha_q(alpha), int(theta_q), _ptr(bits), _ptr(iters)))
+    return bits, iters
+
+
+def lambda_i8(code, lam: int, q: np.ndarray, max_iter: int, alpha: float = 1.0, theta_q: int = 0):
+    """lambda-largest selection per pass (MLP-WBF's bit-choose) with the
+    IMWBF metric, written separately from fwbf_i8."""
+    lib = _load()
+    q = np.ascontiguousarray(q, dtype=np.int8).reshape(-1, code.N)
+    F = q.shape[0]
+    rows, cols = _coo(code)
+    bits = np.zeros((F, (code.N + 31) // 32), dtype=np.uint32)
+    iters = np.zeros(F, dtype=np.int32)
+    _check(lib.oracle_lambda_i8(code.N, code.M, rows.size, _ptr(rows), _ptr(cols), int(lam), _ptr(q), F,
+                                int(max_iter), alpha_q(alpha), int(theta_q), _ptr(bits), _ptr(iters)))
     return bits, iters
 
 

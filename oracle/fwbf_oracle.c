@@ -482,3 +482,92 @@ int oracle_single_flip_i8(int N, int M, int64_t nnz, const int32_t *rows, const 
     free(s);
     return ORACLE_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* lambda-largest selection (Sec. III, MLP-WBF's bit-choose), written on its  */
+/* own                                                                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Per pass: the IMWBF metric of Eq. 1 for every bit (x256, int8 path), then
+ * the lambda bits with the largest metrics -- chosen one after another, each
+ * the largest remaining, lowest index first among equals -- are flipped if
+ * their metric is above theta_q.  All choices read the same syndrome.  lambda = 1
+ * is single-bit flipping; lambda >= N flips every bit with a positive metric.
+ */
+int oracle_lambda_i8(int N, int M, int64_t nnz, const int32_t *rows, const int32_t *cols, int32_t lambda,
+                     const int8_t *q, int64_t n_frames, int32_t max_iter, int32_t alpha_q, int32_t theta_q,
+                     uint32_t *out_bits, int32_t *out_iters) {
+    if (lambda < 1 || max_iter < 1) return ORACLE_EINVAL;
+    ocode c;
+    int rc = ocode_build(N, M, nnz, rows, cols, &c);
+    if (rc) return rc;
+    const int words = (N + 31) / 32;
+    int32_t *a = malloc(sizeof(int32_t) * (size_t)N);
+    uint8_t *z = malloc((size_t)N), *s = malloc((size_t)M), *taken = malloc((size_t)N);
+    int64_t *E = malloc(sizeof(int64_t) * (size_t)N);
+    if (!a || !z || !s || !taken || !E) {
+        rc = ORACLE_ENOMEM;
+        goto done;
+    }
+    for (int64_t f = 0; f < n_frames; ++f) {
+        for (int n = 0; n < N; ++n) {
+            int v = q[f * N + n];
+            a[n] = v < 0 ? -v : v;
+            z[n] = v < 0;
+        }
+        int32_t iters;
+        for (int k = 0;; ++k) {
+            int weight = 0;
+            for (int m = 0; m < M; ++m) {
+                int par = 0;
+                for (int64_t e = c.row_ptr[m]; e < c.row_ptr[m + 1]; ++e) par ^= z[c.row_bit[e]];
+                s[m] = (uint8_t)par;
+                weight += par;
+            }
+            if (weight == 0) {
+                iters = k;
+                break;
+            }
+            if (k == max_iter) {
+                iters = -max_iter;
+                break;
+            }
+            for (int n = 0; n < N; ++n) {
+                int64_t sum = 0;
+                for (int64_t ce = c.col_ptr[n]; ce < c.col_ptr[n + 1]; ++ce) {
+                    const int m = c.col_chk[ce];
+                    int wmin = 1 << 30;
+                    for (int64_t e = c.row_ptr[m]; e < c.row_ptr[m + 1]; ++e) {
+                        const int i = c.row_bit[e];
+                        if (i != n && a[i] < wmin) wmin = a[i];
+                    }
+                    sum += s[m] ? wmin : -wmin;
+                }
+                E[n] = 256 * sum - (int64_t)alpha_q * a[n];
+            }
+            memset(taken, 0, (size_t)N);
+            for (int t = 0; t < lambda && t < N; ++t) {
+                int best = -1;
+                for (int n = 0; n < N; ++n)
+                    if (!taken[n] && (best < 0 || E[n] > E[best])) best = n;
+                if (best < 0 || E[best] <= theta_q) break;
+                taken[best] = 1;
+            }
+            for (int n = 0; n < N; ++n) z[n] ^= taken[n];
+        }
+        uint32_t *ob = out_bits + f * (int64_t)words;
+        memset(ob, 0, sizeof(uint32_t) * (size_t)words);
+        for (int n = 0; n < N; ++n)
+            if (z[n]) ob[n / 32] |= 1u << (n % 32);
+        out_iters[f] = iters;
+    }
+done:
+    free(a);
+    free(z);
+    free(s);
+    free(taken);
+    free(E);
+    ocode_free(&c);
+    return rc;
+}

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
         __syncthreads();
         if (warp < J.warps) {
             unsigned char *ws = smem + J.table_smem_bytes + warp * J.warp_bytes;
-            const int B = J.kind <= kJobGenericCirc ? J.gp.B : J.cp.B;
+            const int B = J.kind <= kJobGenericCirc ? J.gp.nkeys : J.cp.B;
             const uint32_t off_keys = J.kind <= kJobGenericCirc ? J.gp.off_keys : J.cp.off_keys;
             unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + off_keys);
             for (int b = lane; b < B; b += 32) keys[b] = 0ull;

@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(768, 1) fwbf_decode_i8_kernel(const I8Params P
     const int warp = threadIdx.x >> 5;
     unsigned char *ws = smem + P.table_smem_bytes + warp * P.warp_bytes;
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
-    for (int b = lane; b < P.B; b += 32) keys[b] = 0ull;
+    for (int b = lane; b < P.nkeys; b += 32) keys[b] = 0ull;
+    if (P.lambda && lane == 0) *reinterpret_cast<uint32_t *>(ws + P.off_cand + 8u * (uint32_t)P.N) = 0u;
     __syncwarp();
     for (;;) {
         unsigned long long f = 0;
@@ -85,9 +86,10 @@ static inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 // that is already zero on the stream.
 static int launch_generic_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
                              int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
-                             cudaStream_t s) {
+                             cudaStream_t s, int lambda = 0) {
     I8Params P{};
     generic_layout(c, P);
+    if (lambda > 0) generic_layout_lambda(c, P, lambda);
     P.y = y;
     P.F = n_frames;
     P.max_iter = max_iter;
@@ -201,6 +203,29 @@ int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_fr
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-allocation scratch)");
     return launch_i8_with_counter(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters,
                                   static_cast<unsigned long long *>(scratch), s);
+}
+
+}  // namespace fwbf
+
+namespace fwbf {
+
+// lambda-largest selection: the list decoder with a per-frame candidate list
+int launch_decode_i8_lambda(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                            int lambda, uint32_t *out_bits, int32_t *out_iters, cudaStream_t s) {
+    unsigned long long *counter = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(counter, s);
+        return cuda_fail(e, "cudaMemsetAsync");
+    }
+    const int rc =
+        launch_generic_i8(c, y, n_frames, max_iter, alpha_q, 0, out_bits, out_iters, counter, s, lambda);
+    e = cudaFreeAsync(counter, s);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(frame counter)");
+    return 0;
 }
 
 }  // namespace fwbf

@@ -300,6 +300,19 @@ int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
                                   static_cast<cudaStream_t>(stream));
 }
 
+int fwbf_decode_lambda(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, float alpha,
+                       int32_t lambda, uint32_t *out_bits, int32_t *out_iters, void *stream) {
+    int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
+    if (lambda < 1) return fail(FWBF_EINVAL, "lambda must be >= 1");
+    if (lambda > c->N) lambda = c->N;
+    if (n_frames == 0) return FWBF_OK;
+    const int alpha_q = (int)nearbyint((double)alpha * 256.0);
+    return launch_decode_i8_lambda(c, y, n_frames, max_iter, alpha_q, lambda, out_bits, out_iters,
+                                   static_cast<cudaStream_t>(stream));
+}
+
 int fwbf_decode_f32(fwbf_code c, const float *y, int64_t n_frames, int32_t max_iter, float alpha,
                     uint32_t *out_bits, int32_t *out_iters, void *stream) {
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);

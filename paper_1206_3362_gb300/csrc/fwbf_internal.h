@@ -68,6 +68,8 @@ int launch_decode_i8_modes(const fwbf_code_s *c, const int8_t *y, int64_t n_fram
 int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
                              int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
                              cudaStream_t s);
+int launch_decode_i8_lambda(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                            int lambda, uint32_t *out_bits, int32_t *out_iters, cudaStream_t s);
 int launch_decode_f32(const fwbf_code_s *c, const float *y, int64_t n_frames, int max_iter,
                       float alpha, float theta, uint32_t *out_bits, int32_t *out_iters,
                       float *out_E, cudaStream_t s);

@@ -26,7 +26,23 @@ struct I8Params {
     // per-warp shared-memory layout (bytes)
     uint32_t warp_bytes, off_T, off_crec, off_s, off_z, off_keys;
     uint32_t table_smem_bytes;
+    // lambda-largest selection (MLP-WBF's bit-choose) in place of the p-blocks
+    // when lambda > 0: candidates go to a per-frame list, the flip list holds
+    // up to max(B, lambda) bits
+    int lambda;
+    int nkeys;
+    uint32_t off_cand;
 };
+
+// maximum of a 64-bit key over the warp
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, v, d);
+        v = o > v ? o : v;
+    }
+    return v;
+}
 
 // Decodes frame f of P with the calling warp; tbl is the code's table blob
 // (shared or global memory), ws the warp's shared-memory slice.
@@ -43,6 +59,8 @@ __device__ __forceinline__ void generic_frame(const I8Params &P, const uint32_t 
     uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
+    unsigned long long *cand = reinterpret_cast<unsigned long long *>(ws + P.off_cand);  // lambda mode
+    uint32_t *ncand = reinterpret_cast<uint32_t *>(ws + P.off_cand + 8u * (uint32_t)P.N);
     const int N = P.N, M = P.M;
     const uint32_t Z = (uint32_t)P.Z;
     const int Nw = (N + 31) >> 5, Mw = (M + 31) >> 5;
@@ -163,16 +181,37 @@ __device__ __forceinline__ void generic_frame(const I8Params &P, const uint32_t 
             const int tot = (int)(t >> 16);
             const int E = (2 * (int)U - tot) * 256 - P.alpha_q * abs((int)q[n]);
             if (E > P.theta_q) {
-                const uint32_t blk = div_small(n, P.p, P.p_magic);
                 const unsigned long long key =
                     ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - (uint32_t)n);
-                atomicMax(&keys[blk], key);
+                if (P.lambda) {
+                    cand[atomicAdd(ncand, 1u)] = key;
+                } else {
+                    const uint32_t blk = div_small(n, P.p, P.p_magic);
+                    atomicMax(&keys[blk], key);
+                }
             }
         }
         __syncwarp();
+        if (P.lambda) {
+            // the lambda largest candidates, one after another (largest
+            // remaining, lowest index first among equals), into the flip list
+            const int nc = (int)*ncand;
+            int chosen = 0;
+            for (; chosen < P.lambda && chosen < nc; ++chosen) {
+                unsigned long long best = 0ull;
+                for (int i = lane; i < nc; i += 32) best = cand[i] > best ? cand[i] : best;
+                best = warp_max_u64(best);
+                for (int i = lane; i < nc; i += 32)
+                    if (cand[i] == best) cand[i] = 0ull;
+                if (lane == 0) keys[chosen] = best;
+                __syncwarp();
+            }
+            if (lane == 0) *ncand = 0u;
+            __syncwarp();
+        }
         // flips: all blocks read s_k; apply together
         int dW = 0, nflip = 0;
-        for (int b = lane; b < P.B; b += 32) {
+        for (int b = lane; b < P.nkeys; b += 32) {
             const unsigned long long key = keys[b];
             if (key) {
                 keys[b] = 0ull;
@@ -240,7 +279,21 @@ inline void generic_layout(const fwbf_code_s *c, I8Params &P) {
     P.off_z = o;
     o += a16(4 * ((N + 31) / 32));
     P.off_keys = o;
+    P.nkeys = c->B;
     o += a16(8 * (uint32_t)c->B);
+    P.off_cand = o;
+    P.warp_bytes = o;
+}
+
+// Host: adds the lambda-largest candidate list (and a flip list of at least
+// lambda entries) to a layout made by generic_layout.
+inline void generic_layout_lambda(const fwbf_code_s *c, I8Params &P, int lambda) {
+    auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+    P.lambda = lambda;
+    P.nkeys = c->B > lambda ? c->B : lambda;
+    uint32_t o = P.off_keys + a16(8 * (uint32_t)P.nkeys);
+    P.off_cand = o;
+    o += a16(8 * (uint32_t)c->N + 4);
     P.warp_bytes = o;
 }
 

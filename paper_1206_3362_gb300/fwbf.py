@@ -63,6 +63,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_decode": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_decode_noalloc": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_decode_f32": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
+        "fwbf_decode_lambda": ([P, P, i64, i32, f32, i32, P, P, P], ctypes.c_int),
         "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
         "fwbf_decode_sched": ([P, P, i64, i32, P, P, i64, P, P, P, i32, P], ctypes.c_int),
         "fwbf_decode_learned": ([P, P, i64, i32, i32, f32, P, P, P, P, P, i32, P], ctypes.c_int),
@@ -176,6 +177,17 @@ def fwbf_decode_noalloc(code, y, max_iter: int, alpha: float, out_bits, out_iter
     _check(load_library().fwbf_decode_noalloc(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
                                               _dev(out_bits, torch.int32, "out_bits"),
                                               _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
+
+
+def fwbf_decode_lambda(code, y, max_iter: int, alpha: float, lam: int, out_bits, out_iters, stream=None) -> None:
+    """lambda-largest selection per pass with the IMWBF metric (comparison rule)."""
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y, info.N)
+    _check(load_library().fwbf_decode_lambda(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
+                                             int(lam), _dev(out_bits, torch.int32, "out_bits"),
+                                             _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
 
 
 def fwbf_decode_f32(code, y, max_iter: int, alpha: float, out_bits, out_iters, stream=None) -> None:

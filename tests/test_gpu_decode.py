@@ -274,3 +274,21 @@ def test_f32_decisions(fwbf, key, p, ebn0):
     same = (iters == io) & (bits == bo).all(axis=1)
     assert same[clear].all()
     assert clear.mean() > 0.9, f"near-tie frames: {(~clear).sum()}"
+
+
+# ---------------------------------------------------------------------------
+# lambda-largest selection (comparison rule) against the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("key,lam", [("eg255", 1), ("eg255", 10), ("eg1023", 10), ("eg1023", 3),
+                                     ("rand504", 64), ("eg255", 255)])
+def test_lambda_selection_matches_oracle(fwbf, key, lam):
+    h, c, y = frames(key, 160, 3.25, seed=60 + lam)
+    q = oracle.quantize(y)
+    with fwbf.Code.from_parity_check(h, 31 if h.N > 31 else 5) as code:
+        bits, iters = code.outputs(160)
+        fwbf.fwbf_decode_lambda(code.handle, torch.from_numpy(q).cuda(), 30, 1.5, lam, bits, iters)
+        torch.cuda.synchronize()
+    bo, io = oracle.lambda_i8(h, lam, q, 30, alpha=1.5)
+    assert np.array_equal(iters.cpu().numpy(), io)
+    assert np.array_equal(bits.cpu().numpy().view(np.uint32), bo)

@@ -265,3 +265,36 @@ def test_tab1_average_iterations_band():
             _, iters, _ = oracle.fwbf_i8_threaded(h, p, q, 10, alpha=1.5)
             steps = np.where(iters < 0, 11, iters + 1).mean()
             assert abs(steps - tab[key][i]) / tab[key][i] < 0.12, (eb, p, steps)
+
+
+# --------------------------------------------------------------------------
+# lambda-largest selection (MLP-WBF's bit-choose with the IMWBF metric)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("key", ["eg255", "rand504"])
+def test_lambda_one_is_single_flip(key):
+    h, c, y = _noisy(key, 20, 3.0, seed=14)
+    q = oracle.quantize(y)
+    b1, i1 = oracle.lambda_i8(h, 1, q, 30, alpha=1.5)
+    b2, i2 = oracle.single_flip_i8(h, q, 30, alpha=1.5)
+    assert np.array_equal(i1, i2) and np.array_equal(b1, b2)
+
+
+def test_lambda_all_is_p_one():
+    """lambda >= N flips every positive metric, which is FWBF with p = 1."""
+    h, c, y = _noisy("eg255", 20, 2.5, seed=15)
+    q = oracle.quantize(y)
+    b1, i1 = oracle.lambda_i8(h, h.N, q, 25, alpha=1.0)
+    b2, i2 = oracle.fwbf_i8(h, 1, q, 25, alpha=1.0)
+    assert np.array_equal(i1, i2) and np.array_equal(b1, b2)
+
+
+def test_lambda_two_errors():
+    """Two errors in a noiseless EG(15,7) frame: lambda >= 2 corrects both in
+    one pass wherever they are; lambda = 1 needs two passes."""
+    h = make_code("eg15")
+    for j1, j2 in [(0, 1), (3, 11), (7, 14)]:
+        q = np.full((1, 15), 16, dtype=np.int8)
+        q[0, [j1, j2]] = -16
+        assert oracle.lambda_i8(h, 2, q, 10, alpha=1.0)[1][0] == 1
+        assert oracle.lambda_i8(h, 1, q, 10, alpha=1.0)[1][0] == 2
