@@ -396,24 +396,19 @@ def compare_forms(fwbf, h, enc, q, c, w, F, fer_plain, gbps_plain, dev):
 
 
 def e2e(args, fwbf, code, y, w, F, enc, dev, stream):
-    """Same metric through the public API with host buffers: every step copies
-    the float channel values from pinned host memory, quantises, decodes and
-    copies the decisions and pass counts back."""
+    """Same metric through the public host-buffer entry point
+    (fwbf_decode_host): every step copies the float channel values from pinned
+    host memory, quantises, decodes and copies the decisions and pass counts
+    back, chunks pipelined over two streams."""
     import torch
 
     y_host = y.cpu().pin_memory()
     bits_host = torch.empty((F, code.words), dtype=torch.int32).pin_memory()
     iters_host = torch.empty(F, dtype=torch.int32).pin_memory()
-    yd = torch.empty_like(y)
-    qd = torch.empty((F, code.N), dtype=torch.int8, device=dev)
-    bd, idd = code.outputs(F, dev)
 
     def step():
-        yd.copy_(y_host, non_blocking=True)
-        fwbf.fwbf_quantize(yd, qd, stream)
-        fwbf.fwbf_decode(code.handle, qd, w["max_iter"], w["alpha"], bd, idd, stream)
-        bits_host.copy_(bd, non_blocking=True)
-        iters_host.copy_(idd, non_blocking=True)
+        fwbf.fwbf_decode_host(code.handle, y_host, w["max_iter"], w["alpha"], bits_host, iters_host,
+                              chunk_frames=1 << 17, stream=stream)
 
     for _ in range(2):
         step()
@@ -429,7 +424,7 @@ def e2e(args, fwbf, code, y, w, F, enc, dev, stream):
     return {"value": F * enc.K * steps / (ms / 1e3) / 1e9, "unit": "Gb/s",
             "h2d_bytes_per_step": y_host.numel() * 4,
             "d2h_bytes_per_step": bits_host.numel() * 4 + iters_host.numel() * 4,
-            "steps": steps, "ms_per_step": ms / steps}
+            "steps": steps, "ms_per_step": ms / steps, "api": "fwbf_decode_host (2-stream chunk pipeline)"}
 
 
 def cpu_baseline(fwbf, h, enc, q, bits, iters, w):

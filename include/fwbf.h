@@ -130,6 +130,26 @@ int fwbf_decode_noalloc(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
                         float alpha, uint32_t *out_bits, int32_t *out_iters, void *stream);
 
 /*
+ * End to end from host memory: the float channel values of n_frames frames are
+ * copied to the device, quantised (fwbf_quantize) and decoded (fwbf_decode), and
+ * the decisions and pass counts copied back, in chunks of chunk_frames frames
+ * that alternate between two internal streams so that one chunk's copies
+ * overlap another's decoding.  The work is ordered after the work already
+ * queued on `stream`, and `stream` reaches the end of the call only when every
+ * chunk has been copied back (so the caller synchronises on its own stream).
+ *   y_host      host float [n_frames][N] (page-locked for asynchronous copies)
+ *   bits_host   host uint32 [n_frames][ceil(N/32)]
+ *   iters_host  host int32 [n_frames]
+ *   chunk_frames  >= 1 (e.g. 131072); device memory used: 2 chunks of float
+ *               input, int8 frames and outputs, from the stream-ordered
+ *               allocator, released on `stream`.
+ * Host buffers must stay valid until `stream` has completed the call.
+ */
+int fwbf_decode_host(fwbf_code c, const float *y_host, int64_t n_frames, int32_t max_iter,
+                     float alpha, uint32_t *bits_host, int32_t *iters_host,
+                     int64_t chunk_frames, void *stream);
+
+/*
  * Comparison rule: lambda-largest selection (MLP-WBF's bit-choose, Sec. III)
  * with the IMWBF metric of Eq. 1 in place of FWBF's p-blocks.  Every pass
  * computes E'_n for all bits from the same syndrome, takes the lambda bits with

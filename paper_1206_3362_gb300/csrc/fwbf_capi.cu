@@ -300,6 +300,68 @@ int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
                                   static_cast<cudaStream_t>(stream));
 }
 
+int fwbf_decode_host(fwbf_code c, const float *y_host, int64_t n_frames, int32_t max_iter, float alpha,
+                     uint32_t *bits_host, int32_t *iters_host, int64_t chunk_frames, void *stream) {
+    int rc = check_decode_args(c, y_host, n_frames, max_iter, alpha, bits_host, iters_host);
+    if (rc) return rc;
+    if (chunk_frames < 1) return fail(FWBF_EINVAL, "chunk_frames must be >= 1");
+    if (n_frames == 0) return FWBF_OK;
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    const int64_t N = c->N, words = (N + 31) / 32;
+    const int64_t chunk = chunk_frames < n_frames ? chunk_frames : n_frames;
+    // per buffer: float y | int8 q (16-byte aligned) | bits | iters
+    const size_t y_bytes = (size_t)(chunk * N) * 4, q_off = (y_bytes + 255) & ~(size_t)255;
+    const size_t b_off = (q_off + (size_t)(chunk * N) + 255) & ~(size_t)255;
+    const size_t i_off = (b_off + (size_t)(chunk * words) * 4 + 255) & ~(size_t)255;
+    const size_t buf_bytes = (i_off + (size_t)chunk * 4 + 255) & ~(size_t)255;
+    char *dev = nullptr;
+    cudaStream_t st[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_done[2] = {nullptr, nullptr};
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&dev), 2 * buf_bytes, caller);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(host pipeline buffers)");
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaStreamCreateWithFlags(&st[b], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+    // the pipeline starts after the caller's earlier work (and the allocation)
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, caller);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(st[b], ev_start, 0);
+    int64_t i = 0;
+    for (int64_t f0 = 0; f0 < n_frames && e == cudaSuccess && rc == 0; f0 += chunk, ++i) {
+        const int b = (int)(i & 1);
+        const int64_t nf = (n_frames - f0) < chunk ? (n_frames - f0) : chunk;
+        char *base = dev + (size_t)b * buf_bytes;
+        float *yd = reinterpret_cast<float *>(base);
+        int8_t *qd = reinterpret_cast<int8_t *>(base + q_off);
+        uint32_t *bd = reinterpret_cast<uint32_t *>(base + b_off);
+        int32_t *id = reinterpret_cast<int32_t *>(base + i_off);
+        e = cudaMemcpyAsync(yd, y_host + f0 * N, (size_t)(nf * N) * 4, cudaMemcpyHostToDevice, st[b]);
+        if (e != cudaSuccess) break;
+        rc = launch_quantize(yd, qd, nf * N, st[b]);
+        if (rc) break;
+        rc = launch_decode_i8(c, qd, nf, max_iter, (int)nearbyint((double)alpha * 256.0), 0, bd, id, st[b]);
+        if (rc) break;
+        e = cudaMemcpyAsync(bits_host + f0 * words, bd, (size_t)(nf * words) * 4, cudaMemcpyDeviceToHost, st[b]);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(iters_host + f0, id, (size_t)nf * 4, cudaMemcpyDeviceToHost, st[b]);
+    }
+    // join both streams back into the caller's stream, then release
+    for (int b = 0; b < 2; ++b) {
+        if (st[b] && ev_done[b]) {
+            cudaEventRecord(ev_done[b], st[b]);
+            cudaStreamWaitEvent(caller, ev_done[b], 0);
+        }
+    }
+    cudaFreeAsync(dev, caller);
+    for (int b = 0; b < 2; ++b) {
+        if (ev_done[b]) cudaEventDestroy(ev_done[b]);
+        if (st[b]) cudaStreamDestroy(st[b]);
+    }
+    if (ev_start) cudaEventDestroy(ev_start);
+    if (rc) return rc;
+    return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "host pipeline");
+}
+
 int fwbf_decode_lambda(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, float alpha,
                        int32_t lambda, uint32_t *out_bits, int32_t *out_iters, void *stream) {
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);

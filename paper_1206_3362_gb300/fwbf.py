@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_decode_noalloc": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_decode_f32": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_decode_lambda": ([P, P, i64, i32, f32, i32, P, P, P], ctypes.c_int),
+        "fwbf_decode_host": ([P, P, i64, i32, f32, P, P, i64, P], ctypes.c_int),
         "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
         "fwbf_decode_sched": ([P, P, i64, i32, P, P, i64, P, P, P, i32, P], ctypes.c_int),
         "fwbf_decode_learned": ([P, P, i64, i32, i32, f32, P, P, P, P, P, i32, P], ctypes.c_int),
@@ -177,6 +178,32 @@ def fwbf_decode_noalloc(code, y, max_iter: int, alpha: float, out_bits, out_iter
     _check(load_library().fwbf_decode_noalloc(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
                                               _dev(out_bits, torch.int32, "out_bits"),
                                               _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
+
+
+def _host(t, dtype, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def fwbf_decode_host(code, y_host, max_iter: int, alpha: float, bits_host, iters_host,
+                     chunk_frames: int = 1 << 17, stream=None) -> None:
+    """Host float frames -> host decisions, pipelined in chunks over two
+    streams (pinned host tensors give overlapped copies)."""
+    import torch
+
+    info = fwbf_code_query(code)
+    F = _frames(y_host, info.N)
+    _check(load_library().fwbf_decode_host(code, _host(y_host, torch.float32, "y_host"), F, int(max_iter),
+                                           float(alpha), _host(bits_host, torch.int32, "bits_host"),
+                                           _host(iters_host, torch.int32, "iters_host"), int(chunk_frames),
+                                           _stream(stream)))
 
 
 def fwbf_decode_lambda(code, y, max_iter: int, alpha: float, lam: int, out_bits, out_iters, stream=None) -> None:

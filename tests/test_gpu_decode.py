@@ -292,3 +292,21 @@ def test_lambda_selection_matches_oracle(fwbf, key, lam):
     bo, io = oracle.lambda_i8(h, lam, q, 30, alpha=1.5)
     assert np.array_equal(iters.cpu().numpy(), io)
     assert np.array_equal(bits.cpu().numpy().view(np.uint32), bo)
+
+
+def test_decode_host_pipeline(fwbf):
+    """Host float frames in, host decisions out, in chunks over two streams:
+    identical to quantise + decode on the device, for chunk sizes that divide
+    the batch and that leave a ragged last chunk."""
+    h, c, y = frames("eg1023", 1000, 3.75, seed=71)
+    q = oracle.quantize(y)
+    bo, io, _ = oracle.fwbf_i8_threaded(h, 31, q, 100, 1.5)
+    with fwbf.Code.from_parity_check(h, 31) as code:
+        for chunk in (1000, 256, 333, 1):
+            yh = torch.from_numpy(y).pin_memory() if chunk != 333 else torch.from_numpy(y)
+            bh = torch.zeros((1000, code.words), dtype=torch.int32)
+            ih = torch.zeros(1000, dtype=torch.int32)
+            fwbf.fwbf_decode_host(code.handle, yh, 100, 1.5, bh, ih, chunk_frames=chunk)
+            torch.cuda.synchronize()
+            assert np.array_equal(ih.numpy(), io), chunk
+            assert np.array_equal(bh.numpy().view(np.uint32), bo), chunk
