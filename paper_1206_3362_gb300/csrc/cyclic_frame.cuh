@@ -36,7 +36,7 @@ struct CyclicParams {
     int32_t *out_sched;   // [F][k_learn][2] (alpha_q, theta_q) used, or null
     float *out_feat;      // [F][feat_passes][kFeatures] features per pass, or null
     int feat_passes;
-    uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys;
+    uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys, off_red;
 };
 
 __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
@@ -63,16 +63,18 @@ __device__ __forceinline__ void pair_slot(int n, int H, int &idx, int &shift) {
 // Rebuilds the doubled array X2[j] = v(j mod Z) | v((j + H) mod Z) << 16,
 // j < XJ = Z + H - 1, in three index ranges without modulo arithmetic:
 // j < Z - H: (j, j + H); Z - H <= j < Z: (j, j + H - Z); j >= Z: (j - Z, j - Z + H).
+// Thread t of a group of G threads writes every G-th word.
 template <typename F>
-__device__ __forceinline__ void build_doubled(uint32_t *X2, int Z, int H, int XJ, int lane, F v) {
+__device__ __forceinline__ void build_doubled(uint32_t *X2, int Z, int H, int XJ, int t, int G, F v) {
     const int zh = Z - H;
-    for (int j = lane; j < zh; j += 32) X2[j] = v(j) | (v(j + H) << 16);
-    for (int j = zh + lane; j < Z; j += 32) X2[j] = v(j) | (v(j - zh) << 16);
-    for (int j = Z + lane; j < XJ; j += 32) X2[j] = v(j - Z) | (v(j - zh) << 16);
+    for (int j = t; j < zh; j += G) X2[j] = v(j) | (v(j + H) << 16);
+    for (int j = zh + t; j < Z; j += G) X2[j] = v(j) | (v(j - zh) << 16);
+    for (int j = Z + t; j < XJ; j += G) X2[j] = v(j - Z) | (v(j - zh) << 16);
 }
 
 // Adds delta to every half-word of the doubled array that holds position m
-// (the half-words stay in [1, 255], so no carry or borrow crosses halves).
+// (after all updates of a pass the half-words are back in [1, 255]; the
+// additions commute, so updates of several flips may interleave).
 __device__ __forceinline__ void doubled_add(uint32_t *X2, int m, int delta, int Z, int H, int XJ) {
     const uint32_t lo = (uint32_t)delta, hi = (uint32_t)delta * 65536u;
     atomicAdd(&X2[m], lo);
@@ -83,11 +85,72 @@ __device__ __forceinline__ void doubled_add(uint32_t *X2, int m, int delta, int 
     if (jh + Z < XJ) atomicAdd(&X2[jh + Z], hi);
 }
 
-// Decodes frame f of P with the calling warp; d_off / u_off are the code's
-// row / column offsets (shared memory), ws the warp's shared-memory slice.
-template <int R>  // pairs per lane per chunk
+// The WPF warps that decode one frame meet here: the warp itself, or a named
+// barrier (id bar_id, WPF * 32 threads) that also orders their shared memory.
+template <int WPF>
+__device__ __forceinline__ void group_sync(int bar_id) {
+    if constexpr (WPF == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "n"(32 * WPF) : "memory");
+    }
+}
+
+// Sums of three warp-uniform values over the group's warps, through a
+// scratch of 2 x 4 x WPF ints used in alternate halves (a half is rewritten
+// only after the group has met again, so no reader can still be on it).
+template <int WPF>
+__device__ __forceinline__ int3 group_sum3(int3 v, int *red, int &half, int lane, int gw, int bar_id) {
+    if constexpr (WPF == 1) {
+        return v;
+    } else {
+        int *r = red + half * 4 * WPF;
+        half ^= 1;
+        if (lane == 0) {
+            r[4 * gw] = v.x;
+            r[4 * gw + 1] = v.y;
+            r[4 * gw + 2] = v.z;
+        }
+        group_sync<WPF>(bar_id);
+        int3 s = make_int3(0, 0, 0);
+#pragma unroll
+        for (int w = 0; w < WPF; ++w) {
+            s.x += r[4 * w];
+            s.y += r[4 * w + 1];
+            s.z += r[4 * w + 2];
+        }
+        return s;
+    }
+}
+
+// Flip updates of check m for one flipped bit: syndrome toggle (returns the
+// change of the syndrome weight), V' in the doubled array, and the arg-min
+// correction; `old` is the syndrome word before the toggle.
+__device__ __forceinline__ int flip_check(uint32_t *X2, uint32_t *SC, uint32_t rec, uint32_t m, uint32_t old, int Z,
+                                          int H, int XJ) {
+    const uint32_t bit = 1u << (m & 31);
+    const bool now_set = !(old & bit);
+    const uint32_t min1 = rec & 0x7fu, diff = (rec >> 8) & 0x7fu;
+    doubled_add(X2, (int)m, now_set ? 2 * (int)min1 : -2 * (int)min1, Z, H, XJ);
+    if (diff) {
+        int idx, sh;
+        pair_slot((int)(rec >> 16), H, idx, sh);
+        const int d = now_set ? 2 * (int)diff : -2 * (int)diff;
+        atomicAdd(&SC[idx], sh ? (uint32_t)d * 65536u : (uint32_t)d);
+    }
+    return now_set ? 1 : -1;
+}
+
+// Decodes frame f of P with a group of WPF warps (thread t of 32 * WPF);
+// d_off / u_off are the code's row / column offsets (shared memory), ws the
+// group's shared-memory slice, bar_id the group's named barrier (WPF > 1).
+// The check pass and the gather split their chunks over the warps, the flips
+// their blocks; every other loop strides over the group's threads.
+template <int R, int WPF>  // pairs per lane per chunk, warps per frame
 __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32_t *d_off, const uint32_t *u_off,
-                                             unsigned char *ws, int lane, unsigned long long f) {
+                                             unsigned char *ws, int t, int bar_id, unsigned long long f) {
+    constexpr int G = 32 * WPF;
+    const int lane = t & 31, gw = t >> 5;
     int8_t *stage = reinterpret_cast<int8_t *>(ws);
     uint32_t *X2 = reinterpret_cast<uint32_t *>(ws + P.off_X);
     uint32_t *crec = reinterpret_cast<uint32_t *>(ws + P.off_crec);
@@ -97,6 +160,8 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
+    int *red = reinterpret_cast<int *>(ws + P.off_red);
+    int rhalf = 0;
     const int Z = P.Z, H = P.H, DC = P.DC;
     const int Zw = (Z + 31) >> 5;
     const int XJ = Z + H - 1;  // doubled-array words used: i + r <= H - 1 + Z - 1
@@ -113,7 +178,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     const uintptr_t a0 = fb & ~(uintptr_t)15;
     const int off = (int)(fb - a0);
     const int nchunks = (off + Z + 15) >> 4;
-    for (int c = lane; c < nchunks; c += 32) {
+    for (int c = t; c < nchunks; c += G) {
         const uintptr_t src = a0 + (uintptr_t)c * 16;
         uint4 v;
         if (src + 16 <= yend) {
@@ -127,36 +192,37 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         }
         *reinterpret_cast<uint4 *>(stage + c * 16) = v;
     }
-    __syncwarp();
+    group_sync<WPF>(bar_id);
     const int8_t *q = stage + off;
     // frame statistics for the features of scheduled and learned decoding
     float mean_a = 0.0f, weak_frac = 0.0f;
     if (P.mode != kModePlain || P.out_feat) {
         int sa = 0, sw = 0;
-        for (int n = lane; n < Z; n += 32) {
+        for (int n = t; n < Z; n += G) {
             const int a = abs((int)q[n]);
             sa += a;
             sw += a < 8;
         }
-        mean_a = (float)warp_sum(sa) / (127.0f * (float)Z);
-        weak_frac = (float)warp_sum(sw) / (float)Z;
+        const int3 s3 = group_sum3<WPF>(make_int3(warp_sum(sa), warp_sum(sw), 0), red, rhalf, lane, gw, bar_id);
+        mean_a = (float)s3.x / (127.0f * (float)Z);
+        weak_frac = (float)s3.y / (float)Z;
     }
     int iters = 0, passes_before = 0, mode = P.mode;
     for (;;) {  // attempts: the requested mode, then plain FWBF as fallback
-    for (int i = lane; i < H; i += 32) SC[i] = 0x40004000u;
+    for (int i = t; i < H; i += G) SC[i] = 0x40004000u;
 
-    for (int w = 0; w < Zw; ++w) {
+    for (int w = gw; w < Zw; w += WPF) {
         const int n = (w << 5) + lane;
         const uint32_t zb = __ballot_sync(FULL, n < Z && q[n] < 0);
         if (lane == 0) zbits[w] = zb;
     }
-    build_doubled(X2, Z, H, XJ, lane, [&](int n) { return qkey(q[n]); });
-    __syncwarp();
+    build_doubled(X2, Z, H, XJ, t, G, [&](int n) { return qkey(q[n]); });
+    group_sync<WPF>(bar_id);
 
     // ---- check pass: min1/pos, min2 and parity of every check pair; the
     //      signed arg-min corrections (into SC) ----------------------------
     int W = 0;
-    for (int c = 0; c < chunks; ++c) {
+    for (int c = gw; c < chunks; c += WPF) {
         uint32_t k1[R], k2[R], par[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -209,14 +275,15 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
             W += __popc(slo) + __popc(shi);
         }
     }
-    __syncwarp();
+    W = group_sum3<WPF>(make_int3(W, 0, 0), red, rhalf, lane, gw, bar_id).x;  // (meets the group if WPF > 1)
+    if constexpr (WPF == 1) __syncwarp();
 
     // the doubled array of V'_m = (2 s_m - 1) min1_m + 128, kept current
-    build_doubled(X2, Z, H, XJ, lane, [&](int n) {
+    build_doubled(X2, Z, H, XJ, t, G, [&](int n) {
         const uint32_t mn = crec[n] & 0x7fu;
         return ((sbits[n >> 5] >> (n & 31)) & 1u) ? 128u + mn : 128u - mn;
     });
-    __syncwarp();
+    group_sync<WPF>(bar_id);
 
     // ---- iterations ------------------------------------------------------
     const int W0 = W;
@@ -248,7 +315,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
             feat[6] = mean_a;
             feat[7] = weak_frac;
             const int kk = passes_before + k;
-            if (P.out_feat && kk < P.feat_passes && lane == 0) {
+            if (P.out_feat && kk < P.feat_passes && t == 0) {
                 float *o = P.out_feat + (f * (unsigned long long)P.feat_passes + kk) * kFeatures;
 #pragma unroll
                 for (int j = 0; j < kFeatures; ++j) o[j] = feat[j];
@@ -259,11 +326,11 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                 tq = P.sched_t[o];
             } else if (mode == kModeLearned) {
                 float al, th;
-                mlp_eval(P.mlp, feat, lane, al, th);
+                mlp_eval(P.mlp, feat, lane, al, th);  // every warp of the group: identical results
                 th *= 16.0f;
                 aq = __float2int_rn(fminf(fmaxf(al, 0.0f), 64.0f) * 256.0f);
                 tq = __float2int_rn(fminf(fmaxf(th, 0.0f), 4096.0f) * 256.0f);
-                if (P.out_sched && lane == 0) {
+                if (P.out_sched && t == 0) {
                     const unsigned long long o = (f * (unsigned long long)P.k_learn + k) * 2;
                     P.out_sched[o] = aq;
                     P.out_sched[o + 1] = tq;
@@ -275,7 +342,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         int ncand = 0;
         // D_n = sum (2 s_m - 1) w_{n,m} = G_n - 128 d_c + 2 UC_n - TC_n with
         // G the gather of V' over M(n); metric E' = 256 D_n - alpha_q a_n
-        for (int c = 0; c < chunks; ++c) {
+        for (int c = gw; c < chunks; c += WPF) {
             uint32_t acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = 0u;
@@ -305,10 +372,10 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     const int n = i + half * H;
-                    const int G = (int)((G2 >> (16 * half)) & 0xffffu);
+                    const int Gv = (int)((G2 >> (16 * half)) & 0xffffu);
                     const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
                     const int a = abs((int)q[n < Z ? n : 0]);
-                    const int E = (G + sc - bias) * 256 - aq * a;
+                    const int E = (Gv + sc - bias) * 256 - aq * a;
                     if (E > tq && n < Z) {
                         const uint32_t blk = div_small((uint32_t)n, P.p, P.p_magic);
                         const unsigned long long key =
@@ -318,48 +385,52 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                 }
             }
         }
-        __syncwarp();
-        // flips: the warp toggles the checks of one flipped bit at a time and
-        // keeps the syndrome, the doubled V array and the corrections current
+        group_sync<WPF>(bar_id);
+        // flips: warp gw takes the blocks b = gw (mod WPF); a warp toggles the
+        // checks of two flipped bits at a time and keeps the syndrome, the
+        // doubled V array and the corrections current (all by atomics, so the
+        // warps of the group may touch the same words)
         int dW = 0, nflip = 0;
-        for (int b0 = 0; b0 < P.B; b0 += 32) {
-            const int b = b0 + lane;
+        for (int b0 = 0; b0 < P.B; b0 += G) {
+            const int b = b0 + WPF * lane + gw;
             unsigned long long key = 0ull;
             if (b < P.B) {
                 key = keys[b];
                 if (key) keys[b] = 0ull;
             }
+            const uint32_t nmine = 0xffffffffu - (uint32_t)key;
+            if (key) atomicXor(&zbits[nmine >> 5], 1u << (nmine & 31));
             uint32_t pend = __ballot_sync(FULL, key != 0ull);
             nflip += __popc(pend);
             while (pend) {
-                const int src = __ffs(pend) - 1;
+                const int s0 = __ffs(pend) - 1;
                 pend &= pend - 1;
-                const uint32_t n = 0xffffffffu - (uint32_t)__shfl_sync(FULL, key, src);
-                if (lane == 0) zbits[n >> 5] ^= 1u << (n & 31);
+                const bool two = pend != 0u;
+                const int s1 = two ? __ffs(pend) - 1 : s0;
+                if (two) pend &= pend - 1;
+                const uint32_t n0 = __shfl_sync(FULL, nmine, s0);
+                const uint32_t n1 = __shfl_sync(FULL, nmine, s1);
                 for (int e = lane; e < DC; e += 32) {
-                    uint32_t m = n + (e < 32 ? my_u : u_off[e]);
-                    m = m >= (uint32_t)Z ? m - Z : m;
-                    const uint32_t bit = 1u << (m & 31);
-                    const uint32_t old = atomicXor(&sbits[m >> 5], bit);
-                    const bool now_set = !(old & bit);
-                    dW += now_set ? 1 : -1;
-                    const uint32_t rec = crec[m];
-                    const uint32_t min1 = rec & 0x7fu, diff = (rec >> 8) & 0x7fu;
-                    doubled_add(X2, (int)m, now_set ? 2 * (int)min1 : -2 * (int)min1, Z, H, XJ);
-                    if (diff) {
-                        int idx, sh;
-                        pair_slot((int)(rec >> 16), H, idx, sh);
-                        const int d = now_set ? 2 * (int)diff : -2 * (int)diff;
-                        atomicAdd(&SC[idx], sh ? (uint32_t)d * 65536u : (uint32_t)d);
-                    }
+                    const uint32_t u = e < 32 ? my_u : u_off[e];
+                    uint32_t m0 = n0 + u, m1 = n1 + u;
+                    m0 = m0 >= (uint32_t)Z ? m0 - Z : m0;
+                    m1 = m1 >= (uint32_t)Z ? m1 - Z : m1;
+                    const uint32_t old0 = atomicXor(&sbits[m0 >> 5], 1u << (m0 & 31));
+                    const uint32_t old1 = two ? atomicXor(&sbits[m1 >> 5], 1u << (m1 & 31)) : 0u;
+                    const uint32_t rec0 = crec[m0], rec1 = crec[m1];
+                    dW += flip_check(X2, SC, rec0, m0, old0, Z, H, XJ);
+                    if (two) dW += flip_check(X2, SC, rec1, m1, old1, Z, H, XJ);
                 }
             }
         }
+        const int3 tot = group_sum3<WPF>(make_int3(warp_sum(dW), nflip, warp_sum(ncand)), red, rhalf, lane, gw,
+                                         bar_id);
         Wprev = W;
-        W += warp_sum(dW);
+        W += tot.x;
+        nflip = tot.y;
         nflip_prev = nflip;
-        ncand_prev = warp_sum(ncand);
-        __syncwarp();
+        ncand_prev = tot.z;
+        if constexpr (WPF == 1) __syncwarp();
         if (nflip == 0 && mode == kModePlain) {  // fixed point: every later pass repeats this one
             iters = -P.max_iter;
             break;
@@ -371,9 +442,9 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     }  // attempts
 
     uint32_t *ob = P.out_bits + f * (unsigned long long)Zw;
-    for (int w = lane; w < Zw; w += 32) __stcs(ob + w, zbits[w]);
-    if (lane == 0) P.out_iters[f] = iters;
-    __syncwarp();
+    for (int w = t; w < Zw; w += G) __stcs(ob + w, zbits[w]);
+    if (t == 0) P.out_iters[f] = iters;
+    group_sync<WPF>(bar_id);
 }
 
 bool cyclic_eligible(const fwbf_code_s *c);
@@ -405,14 +476,19 @@ inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
     o += a16(4 * ((Z + 31) / 32));
     P.off_keys = o;
     o += a16(8 * (uint32_t)c->B);
+    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 4 warps
+    o += 128;
     P.warp_bytes = o;
     P.table_smem_bytes = a16(c->table_words * 4u);
 }
 
-// pairs per lane per chunk of the packed kernel (a divisor of H / 32)
-inline int cyclic_R(const fwbf_code_s *c) {
+// pairs per lane per chunk of the packed kernel: the largest of 8, 4, 2, 1
+// dividing H / 32 that still gives each of the frame's wpf warps a chunk
+inline int cyclic_R(const fwbf_code_s *c, int wpf = 1) {
     const int ppl = ((c->Z + 1) / 2) / 32;
-    return ppl % 8 == 0 ? 8 : ppl % 4 == 0 ? 4 : ppl % 2 == 0 ? 2 : 1;
+    for (int r = 8; r > 1; r >>= 1)
+        if (ppl % r == 0 && ppl / r >= wpf) return r;
+    return 1;
 }
 
 }  // namespace fwbf

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
     __shared__ uint64_t bars[kMaxJobs];
     __shared__ int flag;
     __shared__ BatchJob J;
-    __shared__ uint32_t d_off[128], u_off[128];
+    __shared__ __align__(16) uint32_t d_off[128], u_off[128];  // read as 8- and 16-byte vectors
     __shared__ int live;
 
     const int lane = threadIdx.x & 31;
@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
             return;
         }
         if (J.kind >= kJobCyclic4) {
-            for (int e = threadIdx.x; e < J.cp.DC; e += blockDim.x) {
-                d_off[e] = st[J.cp.rent_off + e] & 0xffffu;
-                u_off[e] = st[J.cp.cent_off + e] & 0xffffu;
+            for (int e = threadIdx.x; e < 128; e += blockDim.x) {  // zeros past d_c
+                d_off[e] = e < J.cp.DC ? st[J.cp.rent_off + e] & 0xffffu : 0u;
+                u_off[e] = e < J.cp.DC ? st[J.cp.cent_off + e] & 0xffffu : 0u;
             }
         }
         __syncthreads();
@@ -92,10 +92,10 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
                 switch (J.kind) {
                     case kJobGenericPlain: generic_frame<true>(J.gp, st, ws, lane, f); break;
                     case kJobGenericCirc: generic_frame<false>(J.gp, st, ws, lane, f); break;
-                    case kJobCyclic8: cyclic_frame<8>(J.cp, d_off, u_off, ws, lane, f); break;
-                    case kJobCyclic4: cyclic_frame<4>(J.cp, d_off, u_off, ws, lane, f); break;
-                    case kJobCyclic2: cyclic_frame<2>(J.cp, d_off, u_off, ws, lane, f); break;
-                    default: cyclic_frame<1>(J.cp, d_off, u_off, ws, lane, f); break;
+                    case kJobCyclic8: cyclic_frame<8, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
+                    case kJobCyclic4: cyclic_frame<4, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
+                    case kJobCyclic2: cyclic_frame<2, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
+                    default: cyclic_frame<1, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
                 }
             }
         }

@@ -34,12 +34,13 @@ namespace fwbf {
 
 __device__ int g_status_i8_cyclic;
 
-template <int R>  // pairs per lane per chunk
-__global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const CyclicParams P) {
+template <int R, int WPF>  // pairs per lane per chunk, warps per frame
+__global__ void __launch_bounds__(512, WPF == 2 ? 2 : 1) fwbf_decode_i8_cyclic_kernel(const CyclicParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
     __shared__ int flag;
-    __shared__ uint32_t d_off[128], u_off[128];
+    __shared__ __align__(16) uint32_t d_off[128], u_off[128];  // read as 8- and 16-byte vectors
+    __shared__ unsigned long long fslot[16];
 
     {
         uint32_t *st = reinterpret_cast<uint32_t *>(smem);
@@ -47,24 +48,26 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_i8_cyclic_kernel(const Cyc
             if (threadIdx.x == 0) atomicOr(&g_status_i8_cyclic, 1);
             return;
         }
-        for (int e = threadIdx.x; e < P.DC; e += blockDim.x) {
-            d_off[e] = st[P.rent_off + e] & 0xffffu;
-            u_off[e] = st[P.cent_off + e] & 0xffffu;
+        for (int e = threadIdx.x; e < 128; e += blockDim.x) {  // zeros past d_c
+            d_off[e] = e < P.DC ? st[P.rent_off + e] & 0xffffu : 0u;
+            u_off[e] = e < P.DC ? st[P.cent_off + e] & 0xffffu : 0u;
         }
         __syncthreads();
     }
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    unsigned char *ws = smem + P.table_smem_bytes + warp * P.warp_bytes;
+    // groups of WPF warps, one frame each; group g meets at named barrier 1 + g
+    constexpr int G = 32 * WPF;
+    const int t = threadIdx.x % G;
+    const int grp = threadIdx.x / G;
+    const int bar_id = 1 + grp;
+    unsigned char *ws = smem + P.table_smem_bytes + grp * P.warp_bytes;
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
-    for (int b = lane; b < P.B; b += 32) keys[b] = 0ull;
-    __syncwarp();
+    for (int b = t; b < P.B; b += G) keys[b] = 0ull;
     for (;;) {
-        unsigned long long f = 0;
-        if (lane == 0) f = atomicAdd(P.counter, 1ull);
-        f = __shfl_sync(FULL, f, 0);
+        if (t == 0) fslot[grp] = atomicAdd(P.counter, 1ull);
+        group_sync<WPF>(bar_id);
+        const unsigned long long f = fslot[grp];  // rewritten only after the frame's last meeting
         if (f >= (unsigned long long)P.F) break;
-        cyclic_frame<R>(P, d_off, u_off, ws, lane, f);
+        cyclic_frame<R, WPF>(P, d_off, u_off, ws, t, bar_id, f);
     }
 }
 
@@ -120,31 +123,37 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     const uint32_t optin = (uint32_t)c->smem_optin;
     const uint32_t reserve = 2048u;  // static shared memory of the kernel
     if (P.table_smem_bytes + P.warp_bytes + reserve > optin)
-        return fail(FWBF_EUNSUPPORTED, "cyclic code too large for one warp's shared memory");
-    int warps = (int)((optin - reserve - P.table_smem_bytes) / P.warp_bytes);
-    if (warps > 16) warps = 16;
-    const uint32_t dyn = P.table_smem_bytes + warps * P.warp_bytes;
-
-    const int pairs_per_lane = P.H / 32;
+        return fail(FWBF_EUNSUPPORTED, "cyclic code too large for one block's shared memory");
+    // frames whose slices fit in one block; with 16 or more, two blocks of 8
+    // frames per SM and two warps per frame (32 warps, 64 registers each);
+    // otherwise one block and four warps per frame
+    const int fmax = (int)((optin - reserve - P.table_smem_bytes) / P.warp_bytes);
+    const int wpf = fmax >= 8 ? 2 : 4;
+    int frames = wpf == 2 ? (fmax >= 16 ? 8 : fmax / 2) : (fmax < 4 ? fmax : 4);
+    const int R = cyclic_R(c, wpf);
     void (*kern)(const CyclicParams);
-    if (pairs_per_lane % 8 == 0)
-        kern = fwbf_decode_i8_cyclic_kernel<8>;
-    else if (pairs_per_lane % 4 == 0)
-        kern = fwbf_decode_i8_cyclic_kernel<4>;
-    else if (pairs_per_lane % 2 == 0)
-        kern = fwbf_decode_i8_cyclic_kernel<2>;
+    if (wpf == 2)
+        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 2> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 2>
+             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 2> : fwbf_decode_i8_cyclic_kernel<1, 2>;
     else
-        kern = fwbf_decode_i8_cyclic_kernel<1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 4> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 4>
+             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 4> : fwbf_decode_i8_cyclic_kernel<1, 4>;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, dyn);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm < 1) return fail(FWBF_EUNSUPPORTED, "cyclic decode kernel does not fit on an SM");
+    uint32_t dyn = 0;
+    cudaError_t e = cudaSuccess;
+    for (; frames >= 1; --frames) {  // shrink the block until the occupancy calculator places one
+        dyn = P.table_smem_bytes + frames * P.warp_bytes;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, frames * wpf * 32, dyn);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (per_sm >= 1) break;
+    }
+    if (frames < 1 || per_sm < 1) return fail(FWBF_EUNSUPPORTED, "cyclic decode kernel does not fit on an SM");
     int64_t blocks = (int64_t)per_sm * c->num_sms;
-    const int64_t need = (n_frames + warps - 1) / warps;
+    const int64_t need = (n_frames + frames - 1) / frames;
     if (blocks > need) blocks = need;
-    kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
+    kern<<<(unsigned)blocks, frames * wpf * 32, dyn, s>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "decode_i8_cyclic launch");
     return 0;
