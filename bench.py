@@ -35,10 +35,11 @@ SM_MAX_MHZ = 2070.0
 WORKLOAD = dict(code="eg1023", ebn0_db=4.0, frames=1 << 20, max_iter=100, seg_len=31, alpha=1.5)
 
 # DRAM bytes (read + write) per frame of the decode kernel from one ncu capture
-# (fwbf_decode_i8_cyclic_kernel<8>, 131,072 frames of this workload; scaled by
+# (fwbf_decode_i8_cyclic_kernel<8, 2>, 131,072 frames of this workload; scaled by
 # frames, since traffic is the frame bytes in and the decisions out); see
 # profiles/fwbf_decode_i8_eg1023_4dB.md.  Set to None when the kernel changes.
-DECODE_TRAFFIC_BYTES_PER_FRAME = 142.585344e6 / 131072
+DECODE_TRAFFIC_BYTES_PER_FRAME = (134.258688e6 + 8.962048e6) / 131072
+DECODE_KERNEL = "fwbf_decode_i8_cyclic_kernel<8, 2>"
 
 
 def parse():
@@ -48,6 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=WORKLOAD["frames"])
+    ap.add_argument("--no-peak", action="store_true", help="skip the integer issue-rate measurement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="eg1023", choices=["eg1023", "batched4"],
@@ -216,6 +218,9 @@ def main():
         fwbf.fwbf_quantize(y, q, stream)
         fwbf.fwbf_decode(code.handle, q, w["max_iter"], w["alpha"], bits, iters, stream)
 
+    # measured integer issue rate of this GPU (the roofline's measured denominator)
+    peak_meas = fwbf.fwbf_peak_int_issue(1, 200.0, stream) / 1e12 if not args.no_peak else None
+
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -271,8 +276,11 @@ def main():
                      "frac": achieved / peak,
                      "traffic": (DECODE_TRAFFIC_BYTES_PER_FRAME * F if DECODE_TRAFFIC_BYTES_PER_FRAME else None),
                      "algorithmic_bytes": F * (N + 4 * ((N + 31) // 32) + 4),
-                     "kernel": "fwbf_decode_i8_cyclic_kernel<8>", "decode_ms": dec_ms,
-                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (derived)"},
+                     "kernel": DECODE_KERNEL, "decode_ms": dec_ms,
+                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (derived)",
+                     "peak_measured": peak_meas, "frac_of_measured": achieved / peak_meas if peak_meas else None,
+                     "peak_measured_basis": "fwbf_peak_int_issue(mix=1): logic ops and integer multiply-adds "
+                                            "alternating, 64 warps/SM, on this GPU before the timed region"},
         "gpu_launches": 2 * args.steps,
         "clocks": clock_info,
     }

@@ -65,6 +65,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_decode_f32": ([P, P, i64, i32, f32, P, P, P], ctypes.c_int),
         "fwbf_decode_lambda": ([P, P, i64, i32, f32, i32, P, P, P], ctypes.c_int),
         "fwbf_decode_host": ([P, P, i64, i32, f32, P, P, i64, P], ctypes.c_int),
+        "fwbf_peak_int_issue": ([ctypes.c_int, ctypes.c_double, P, P, P], ctypes.c_int),
         "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
         "fwbf_decode_sched": ([P, P, i64, i32, P, P, i64, P, P, P, i32, P], ctypes.c_int),
         "fwbf_decode_learned": ([P, P, i64, i32, i32, f32, P, P, P, P, P, i32, P], ctypes.c_int),
@@ -204,6 +205,14 @@ def fwbf_decode_host(code, y_host, max_iter: int, alpha: float, bits_host, iters
                                            float(alpha), _host(bits_host, torch.int32, "bits_host"),
                                            _host(iters_host, torch.int32, "iters_host"), int(chunk_frames),
                                            _stream(stream)))
+
+
+def fwbf_peak_int_issue(mix: int, ms: float = 200.0, stream=None) -> float:
+    """Measured integer issue rate of the current GPU, lane-operations per
+    second (mix 0: logic ops only; mix 1: logic ops and multiply-adds)."""
+    r = ctypes.c_double(0.0)
+    _check(load_library().fwbf_peak_int_issue(int(mix), float(ms), _stream(stream), ctypes.byref(r), None))
+    return r.value
 
 
 def fwbf_decode_lambda(code, y, max_iter: int, alpha: float, lam: int, out_bits, out_iters, stream=None) -> None:

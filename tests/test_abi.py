@@ -110,3 +110,14 @@ def test_binding_fails_loudly_without_library(tmp_path):
             fwbf.load_library(str(tmp_path / "missing.so"))
     finally:
         fwbf._lib = saved
+
+
+def test_peak_probe_rejects_bad_arguments(lib):
+    """The integer issue-rate microbenchmark validates its arguments on the
+    host before any CUDA call."""
+    from paper_1206_3362_gb300 import fwbf
+
+    r = ctypes.c_double(0.0)
+    assert lib.fwbf_peak_int_issue(2, 100.0, None, ctypes.byref(r), None) == fwbf.FWBF_EINVAL
+    assert lib.fwbf_peak_int_issue(1, 0.5, None, ctypes.byref(r), None) == fwbf.FWBF_EINVAL
+    assert lib.fwbf_peak_int_issue(1, 100.0, None, None, None) == fwbf.FWBF_EINVAL
