@@ -61,17 +61,23 @@ def calibration_frames(h, enc, F, ebn0, seed, device="cuda"):
     return fwbf.quantize(y), c
 
 
-def _frame_errors(bits, iters, c):
-    from .learned import frame_ok
+def _errors(bits, iters, c):
+    """(frame errors, bit errors) against the transmitted codewords."""
+    from .learned import frame_ok, unpack_bits_torch
 
-    return int((~frame_ok(bits, iters, c)).sum().item())
+    fe = int((~frame_ok(bits, iters, c)).sum().item())
+    be = int((unpack_bits_torch(bits, c.shape[1]) != c).sum().item())
+    return fe, be
 
 
 def tune_code(h, enc, ebn0: float, p_ref: int, alpha_ref: float = 1.5, frames: int = 1 << 15,
               max_iter: int = 100, p_candidates=P_CANDIDATES, alpha_candidates=ALPHA_CANDIDATES,
               seed: int = 4242, log=None):
-    """Best FER-qualified (p, alpha) for one code; returns a dict with the
-    choice, the reference and every candidate measured."""
+    """Fastest (p, alpha) for one code among the candidates with no more frame
+    errors and no more bit errors than the reference (p_ref, alpha_ref) on the
+    same seeded frames (bit errors decide between settings that all fail, as on
+    codes beyond bit flipping's reach); returns a dict with the choice, the
+    reference and every candidate measured."""
     q, c = calibration_frames(h, enc, frames, ebn0, seed)
     results = []
     ref = None
@@ -80,14 +86,15 @@ def tune_code(h, enc, ebn0: float, p_ref: int, alpha_ref: float = 1.5, frames: i
         with fwbf.Code.from_parity_check(h, p) as code:
             bits, iters = code.outputs(frames)
             ms = _time(lambda: fwbf.fwbf_decode(code.handle, q, max_iter, a, bits, iters))
-            fe = _frame_errors(bits, iters, c)
-        r = {"p": p, "alpha": a, "frame_errors": fe, "ms": ms}
+            fe, be = _errors(bits, iters, c)
+        r = {"p": p, "alpha": a, "frame_errors": fe, "bit_errors": be, "ms": ms}
         results.append(r)
         if (p, a) == (p_ref, alpha_ref):
             ref = r
         if log:
             log(r)
-    qualified = [r for r in results if r["frame_errors"] <= ref["frame_errors"]]
+    qualified = [r for r in results
+                 if r["frame_errors"] <= ref["frame_errors"] and r["bit_errors"] <= ref["bit_errors"]]
     best = min(qualified, key=lambda r: r["ms"])
     return {"choice": {"p": best["p"], "alpha": best["alpha"]}, "reference": ref, "candidates": results,
             "frames": frames, "ebn0_db": ebn0}
@@ -123,7 +130,7 @@ class Cache:
     def key(self, h, ebn0, what="code"):
         import torch
 
-        return f"{what}:{code_key(h)}:{ebn0:.3f}:{torch.cuda.get_device_name()}"
+        return f"{what}:v2:{code_key(h)}:{ebn0:.3f}:{torch.cuda.get_device_name()}"  # v2: frame + bit errors
 
     def get(self, k):
         return self.data.get(k)

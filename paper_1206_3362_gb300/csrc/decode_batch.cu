@@ -27,11 +27,12 @@ namespace fwbf {
 __device__ int g_status_batch;
 
 enum JobKind : int { kJobGenericPlain = 0, kJobGenericCirc = 1, kJobCyclic4 = 2, kJobCyclic8 = 3, kJobCyclic2 = 4,
-                     kJobCyclic1 = 5 };
+                     kJobCyclic1 = 5, kJobCyclic8W2 = 6, kJobCyclic8W4 = 7 };
 
 struct BatchJob {
     int kind;
     int warps;  // warps of a CTA that decode this job (shared memory permitting)
+    int wpf;    // warps per frame (codes whose frames fill the CTA's shared memory before its warps)
     uint32_t table_smem_bytes;
     uint32_t warp_bytes;
     unsigned long long *counter;
@@ -42,6 +43,54 @@ struct BatchJob {
 
 constexpr int kMaxJobs = 16;
 
+// The CTA's frames of a cyclic job decoded by groups of WPF warps (group g
+// meets at named barrier 1 + g; the CTA-wide barrier 0 is not used meanwhile).
+template <int WPF>
+__device__ __forceinline__ void batch_cyclic_groups(const BatchJob &J, const uint32_t *d_off, const uint32_t *u_off,
+                                                    unsigned char *smem, unsigned long long *fslot) {
+    constexpr int G = 32 * WPF;
+    const int t = threadIdx.x % G, grp = threadIdx.x / G, bar_id = 1 + grp;
+    unsigned char *ws = smem + J.table_smem_bytes + grp * J.warp_bytes;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + J.cp.off_keys);
+    for (int b = t; b < J.cp.B; b += G) keys[b] = 0ull;
+    for (;;) {
+        if (t == 0) fslot[grp] = atomicAdd(J.counter, 1ull);
+        group_sync<WPF>(bar_id);
+        const unsigned long long f = fslot[grp];
+        if (f >= (unsigned long long)J.F) break;
+        cyclic_frame<8, WPF>(J.cp, d_off, u_off, ws, t, bar_id, f);
+    }
+}
+
+// The same for a job of the list decoder (tbl: the code's staged tables).
+template <bool PLAIN, int WPF>
+__device__ __forceinline__ void batch_generic_groups(const BatchJob &J, const uint32_t *tbl, unsigned char *smem,
+                                                     unsigned long long *fslot) {
+    constexpr int G = 32 * WPF;
+    const int t = threadIdx.x % G, grp = threadIdx.x / G, bar_id = 1 + grp;
+    unsigned char *ws = smem + J.table_smem_bytes + grp * J.warp_bytes;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + J.gp.off_keys);
+    for (int b = t; b < J.gp.nkeys; b += G) keys[b] = 0ull;
+    for (;;) {
+        if (t == 0) fslot[grp] = atomicAdd(J.counter, 1ull);
+        group_sync<WPF>(bar_id);
+        const unsigned long long f = fslot[grp];
+        if (f >= (unsigned long long)J.F) break;
+        generic_frame<PLAIN, WPF>(J.gp, tbl, ws, t, bar_id, f);
+    }
+}
+
+template <bool PLAIN>
+__device__ __forceinline__ void batch_generic_dispatch(const BatchJob &J, const uint32_t *tbl, unsigned char *smem,
+                                                       unsigned long long *fslot) {
+    if (J.wpf == 2)
+        batch_generic_groups<PLAIN, 2>(J, tbl, smem, fslot);
+    else if (J.wpf == 4)
+        batch_generic_groups<PLAIN, 4>(J, tbl, smem, fslot);
+    else
+        batch_generic_groups<PLAIN, 8>(J, tbl, smem, fslot);
+}
+
 __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJob *__restrict__ jobs, int n_jobs) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bars[kMaxJobs];
@@ -49,6 +98,7 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
     __shared__ BatchJob J;
     __shared__ __align__(16) uint32_t d_off[128], u_off[128];  // read as 8- and 16-byte vectors
     __shared__ int live;
+    __shared__ unsigned long long fslot[16];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -77,7 +127,16 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
             }
         }
         __syncthreads();
-        if (warp < J.warps) {
+        if (warp < J.warps && J.wpf > 1) {
+            if (J.kind == kJobCyclic8W2)
+                batch_cyclic_groups<2>(J, d_off, u_off, smem, fslot);
+            else if (J.kind == kJobCyclic8W4)
+                batch_cyclic_groups<4>(J, d_off, u_off, smem, fslot);
+            else if (J.kind == kJobGenericPlain)
+                batch_generic_dispatch<true>(J, st, smem, fslot);
+            else
+                batch_generic_dispatch<false>(J, st, smem, fslot);
+        } else if (warp < J.warps) {
             unsigned char *ws = smem + J.table_smem_bytes + warp * J.warp_bytes;
             const int B = J.kind <= kJobGenericCirc ? J.gp.nkeys : J.cp.B;
             const uint32_t off_keys = J.kind <= kJobGenericCirc ? J.gp.off_keys : J.cp.off_keys;
@@ -90,8 +149,8 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
                 f = __shfl_sync(FULL, f, 0);
                 if (f >= (unsigned long long)J.F) break;
                 switch (J.kind) {
-                    case kJobGenericPlain: generic_frame<true>(J.gp, st, ws, lane, f); break;
-                    case kJobGenericCirc: generic_frame<false>(J.gp, st, ws, lane, f); break;
+                    case kJobGenericPlain: generic_frame<true, 1>(J.gp, st, ws, lane, 0, f); break;
+                    case kJobGenericCirc: generic_frame<false, 1>(J.gp, st, ws, lane, 0, f); break;
                     case kJobCyclic8: cyclic_frame<8, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
                     case kJobCyclic4: cyclic_frame<4, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
                     case kJobCyclic2: cyclic_frame<2, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
@@ -184,9 +243,20 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         b.F = in.n_frames;
         if (b.table_smem_bytes + b.warp_bytes + reserve > (uint32_t)optin)
             return fail(FWBF_EUNSUPPORTED, "a job's code does not fit one warp's shared memory");
-        b.warps = (int)(((uint32_t)optin - reserve - b.table_smem_bytes) / b.warp_bytes);
-        if (b.warps > warps_per_cta) b.warps = warps_per_cta;
-        const uint32_t need = b.table_smem_bytes + b.warps * b.warp_bytes;
+        int frames = (int)(((uint32_t)optin - reserve - b.table_smem_bytes) / b.warp_bytes);
+        if (frames > warps_per_cta) frames = warps_per_cta;
+        // codes whose frames fill the shared memory before the warps run out:
+        // 2 or 4 warps per frame (packed R = 8 decoder), 2, 4 or 8 (list decoder)
+        b.wpf = 1;
+        const int spare = warps_per_cta / frames;
+        if (b.kind == kJobCyclic8) {
+            b.wpf = spare >= 4 ? 4 : spare >= 2 ? 2 : 1;
+            if (b.wpf > 1) b.kind = b.wpf == 4 ? kJobCyclic8W4 : kJobCyclic8W2;
+        } else if (b.kind <= kJobGenericCirc) {
+            b.wpf = spare >= 8 ? 8 : spare >= 4 ? 4 : spare >= 2 ? 2 : 1;
+        }
+        b.warps = frames * b.wpf;
+        const uint32_t need = b.table_smem_bytes + frames * b.warp_bytes;
         if (need > dyn) dyn = need;
     }
     fwbf_batch_s *bh = new (std::nothrow) fwbf_batch_s();

@@ -35,11 +35,12 @@ namespace fwbf {
 
 __device__ int g_status_i8;
 
-template <bool PLAIN>  // PLAIN: Z == 1, the tables are plain CSR / CSC
+template <bool PLAIN, int WPF>  // PLAIN: Z == 1, the tables are plain CSR / CSC; warps per frame
 __global__ void __launch_bounds__(768, 1) fwbf_decode_i8_kernel(const I8Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
     __shared__ int flag;
+    __shared__ unsigned long long fslot[24];
 
     const uint32_t *tbl = P.table;
     if (P.table_in_smem) {
@@ -50,19 +51,21 @@ __global__ void __launch_bounds__(768, 1) fwbf_decode_i8_kernel(const I8Params P
         }
         tbl = st;
     }
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    unsigned char *ws = smem + P.table_smem_bytes + warp * P.warp_bytes;
+    // groups of WPF warps, one frame each; group g meets at named barrier 1 + g
+    constexpr int G = 32 * WPF;
+    const int t = threadIdx.x % G;
+    const int grp = threadIdx.x / G;
+    const int bar_id = 1 + grp;
+    unsigned char *ws = smem + P.table_smem_bytes + grp * P.warp_bytes;
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
-    for (int b = lane; b < P.nkeys; b += 32) keys[b] = 0ull;
-    if (P.lambda && lane == 0) *reinterpret_cast<uint32_t *>(ws + P.off_cand + 8u * (uint32_t)P.N) = 0u;
-    __syncwarp();
+    for (int b = t; b < P.nkeys; b += G) keys[b] = 0ull;
+    if (P.lambda && t == 0) *reinterpret_cast<uint32_t *>(ws + P.off_cand + 8u * (uint32_t)P.N) = 0u;
     for (;;) {
-        unsigned long long f = 0;
-        if (lane == 0) f = atomicAdd(P.counter, 1ull);
-        f = __shfl_sync(FULL, f, 0);
+        if (t == 0) fslot[grp] = atomicAdd(P.counter, 1ull);
+        group_sync<WPF>(bar_id);
+        const unsigned long long f = fslot[grp];  // rewritten only after the frame's last meeting
         if (f >= (unsigned long long)P.F) break;
-        generic_frame<PLAIN>(P, tbl, ws, lane, f);
+        generic_frame<PLAIN, WPF>(P, tbl, ws, t, bar_id, f);
     }
 }
 
@@ -101,25 +104,36 @@ static int launch_generic_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_fr
 
     const uint32_t tbytes = c->table_words * 4u;
     const uint32_t optin = (uint32_t)c->smem_optin;
-    P.table_in_smem = (tbytes + P.warp_bytes + 256u <= optin && tbytes <= 96u * 1024u) ? 1 : 0;
+    const uint32_t margin = 512u;  // static shared memory of the kernel
+    P.table_in_smem = (tbytes + P.warp_bytes + margin <= optin && tbytes <= 96u * 1024u) ? 1 : 0;
     P.table_smem_bytes = P.table_in_smem ? tbytes : 0;
-    const uint32_t avail = optin - 256u - P.table_smem_bytes;  // static shared memory margin
-    if (P.warp_bytes > avail) return fail(FWBF_EUNSUPPORTED, "code too large for one warp's shared memory");
-    int warps = (int)(avail / P.warp_bytes);
-    if (warps > 24) warps = 24;
-    const uint32_t dyn = P.table_smem_bytes + warps * P.warp_bytes;
+    const uint32_t avail = optin - margin - P.table_smem_bytes;
+    if (P.warp_bytes > avail) return fail(FWBF_EUNSUPPORTED, "code too large for one block's shared memory");
+    int frames = (int)(avail / P.warp_bytes);
+    if (frames > 24) frames = 24;
+    // up to 24 warps per block: codes with fewer frames per block than that
+    // get 2, 4 or 8 warps per frame (lambda-largest selection keeps one)
+    int wpf = 1;
+    while (lambda == 0 && wpf < 8 && frames * wpf * 2 <= 24) wpf *= 2;
+    const uint32_t dyn = P.table_smem_bytes + frames * P.warp_bytes;
 
-    auto kern = c->Z == 1 ? fwbf_decode_i8_kernel<true> : fwbf_decode_i8_kernel<false>;
+    void (*kern)(const I8Params);
+    if (c->Z == 1)
+        kern = wpf == 1 ? fwbf_decode_i8_kernel<true, 1> : wpf == 2 ? fwbf_decode_i8_kernel<true, 2>
+             : wpf == 4 ? fwbf_decode_i8_kernel<true, 4> : fwbf_decode_i8_kernel<true, 8>;
+    else
+        kern = wpf == 1 ? fwbf_decode_i8_kernel<false, 1> : wpf == 2 ? fwbf_decode_i8_kernel<false, 2>
+             : wpf == 4 ? fwbf_decode_i8_kernel<false, 4> : fwbf_decode_i8_kernel<false, 8>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, frames * wpf * 32, dyn);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) return fail(FWBF_EUNSUPPORTED, "decode kernel does not fit on an SM");
     int64_t blocks = (int64_t)per_sm * c->num_sms;
-    const int64_t need = (n_frames + warps - 1) / warps;
+    const int64_t need = (n_frames + frames - 1) / frames;
     if (blocks > need) blocks = need;
-    kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
+    kern<<<(unsigned)blocks, frames * wpf * 32, dyn, s>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "decode_i8 launch");
     return 0;

@@ -106,4 +106,42 @@ __device__ __forceinline__ bool stage_table(uint32_t *dst, const uint32_t *src, 
 
 __device__ __forceinline__ int warp_sum(int v) { return __reduce_add_sync(FULL, v); }
 
+// The WPF warps that decode one frame meet here: the warp itself, or a named
+// barrier (id bar_id, WPF * 32 threads) that also orders their shared memory.
+template <int WPF>
+__device__ __forceinline__ void group_sync(int bar_id) {
+    if constexpr (WPF == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "n"(32 * WPF) : "memory");
+    }
+}
+
+// Sums of three warp-uniform values over the group's warps, through a
+// scratch of 2 x 4 x WPF ints used in alternate halves (a half is rewritten
+// only after the group has met again, so no reader can still be on it).
+template <int WPF>
+__device__ __forceinline__ int3 group_sum3(int3 v, int *red, int &half, int lane, int gw, int bar_id) {
+    if constexpr (WPF == 1) {
+        return v;
+    } else {
+        int *r = red + half * 4 * WPF;
+        half ^= 1;
+        if (lane == 0) {
+            r[4 * gw] = v.x;
+            r[4 * gw + 1] = v.y;
+            r[4 * gw + 2] = v.z;
+        }
+        group_sync<WPF>(bar_id);
+        int3 s = make_int3(0, 0, 0);
+#pragma unroll
+        for (int w = 0; w < WPF; ++w) {
+            s.x += r[4 * w];
+            s.y += r[4 * w + 1];
+            s.z += r[4 * w + 2];
+        }
+        return s;
+    }
+}
+
 }  // namespace fwbf

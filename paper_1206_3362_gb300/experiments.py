@@ -10,12 +10,22 @@
   Eb/N0 for two block lengths and K_max = 5 and 10 (the paper notes that 5 and 10
   iterations are not distinctly apart).
 
+* ``scale4``: learned + batched at scale: the rate-0.94 quasi-cyclic N = 16384
+  code (column weight 4, circulants of 512) and EG(4095,3367), 2^22 frames over
+  4.0-5.5 dB, one graph-captured batched launch with autotuned block lengths
+  and the learned schedule on the EG code, against plain FWBF (paper setting,
+  one launch per code and point) on the same frames.  Frames reuse a pool of
+  seeded codewords under fresh seeded noise (FWBF's outcome depends only on the
+  error pattern and |y|, not on which codeword was sent).
+
     python -m paper_1206_3362_gb300.experiments tab1 [--frames N]
     python -m paper_1206_3362_gb300.experiments eg255 [--frames N]
+    python -m paper_1206_3362_gb300.experiments scale4 [--frames N]
 """
 from __future__ import annotations
 
 import json
+import os
 
 from . import fwbf
 from .learned import frame_ok, make_frames, unpack_bits_torch, wilson
@@ -74,6 +84,156 @@ def eg255(frames: int = 1 << 17, alpha: float = 1.5, ebn0=(3.0, 3.5, 4.0, 4.5, 5
     return out
 
 
+SCALE4_CODES = (("qc16384", 32), ("eg4095", 64))  # (code, the paper-setting block length p)
+SCALE4_EBN0 = (4.0, 4.5, 5.0, 5.5)
+
+
+def _pool_frames(enc, pool_c, n, ebn0, seed, device, chunk=1 << 15):
+    """n quantised frames: codeword pool_c[i mod P] plus fresh seeded AWGN."""
+    import torch
+
+    from .inputs.channel import awgn_sigma
+
+    P, N = pool_c.shape
+    q = torch.empty((n, N), dtype=torch.int8, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + int(round(ebn0 * 1000)))
+    sigma = awgn_sigma(ebn0, enc.rate)
+    for s0 in range(0, n, chunk):
+        m = min(chunk, n - s0)
+        idx = torch.arange(s0, s0 + m, device=device) % P
+        y = (1.0 - 2.0 * pool_c[idx].to(torch.float32)) + sigma * torch.randn((m, N), generator=g, device=device)
+        fwbf.fwbf_quantize(y.contiguous(), q[s0:s0 + m])
+    return q
+
+
+def _errors(bits, iters, pool_c, chunk=1 << 15):
+    import torch
+
+    from .learned import unpack_bits_torch
+
+    P, N = pool_c.shape
+    fe = be = 0
+    for s0 in range(0, bits.shape[0], chunk):
+        b = bits[s0:s0 + chunk]
+        idx = torch.arange(s0, s0 + b.shape[0], device=bits.device) % P
+        wrong = unpack_bits_torch(b, N) != pool_c[idx]
+        fe += int((wrong.any(dim=1) | (iters[s0:s0 + chunk] < 0)).sum().item())
+        be += int(wrong.sum().item())
+    return fe, be
+
+
+def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, max_iter: int = 100):
+    import time
+
+    import torch
+
+    from . import autotune
+    from .inputs import Encoder, make_code
+    from .inputs.channel import random_codewords_torch
+    from .learned import Network, weights_path
+
+    dev = "cuda"
+    per_job = frames // (len(SCALE4_CODES) * len(SCALE4_EBN0))
+    jobs, handles = [], []
+    out = {"frames": per_job * len(SCALE4_CODES) * len(SCALE4_EBN0), "frames_per_job": per_job,
+           "ebn0_db": SCALE4_EBN0, "max_iter": max_iter, "codes": {}, "jobs": []}
+    t0 = time.time()
+    for ci, (key, p_ref) in enumerate(SCALE4_CODES):
+        h = make_code(key)
+        enc = Encoder(h)
+        pool = 1 << 13 if h.N > 8192 else 1 << 14
+        _, pool_c = random_codewords_torch(enc, pool, seed=4000 + ci, device=dev)
+        tune = autotune.tune_code(h, enc, SCALE4_EBN0[1], p_ref=p_ref, alpha_ref=1.5, frames=1 << 14)
+        p_t, a_t = tune["choice"]["p"], tune["choice"]["alpha"]
+        net, k_learn = None, 0
+        wpath = (weights or {}).get(key, weights_path(key))
+        if os.path.exists(wpath):
+            net = Network(alpha_default=a_t)
+            meta = net.load(wpath)
+            p_t, a_t, k_learn = int(meta["seg_len"]), float(meta["alpha_default"]), int(meta["k_learn"])
+        code_ref = fwbf.Code.from_parity_check(h, p_ref)
+        code_t = fwbf.Code.from_parity_check(h, p_t)
+        handles += [code_ref, code_t]
+        out["codes"][key] = {"N": h.N, "K": enc.K, "rate": enc.rate, "p_paper": p_ref, "p_tuned": p_t,
+                             "alpha_tuned": a_t, "learned": net is not None, "k_learn": k_learn,
+                             "codeword_pool": pool, "autotune": tune["choice"]}
+        for pi, eb in enumerate(SCALE4_EBN0):
+            q = _pool_frames(enc, pool_c, per_job, eb, seed=5000 + 10 * ci + pi, device=dev)
+            jobs.append(dict(key=key, ebn0=eb, K=enc.K, q=q, pool_c=pool_c, code_ref=code_ref, code_t=code_t,
+                             a_t=a_t, net=net, k_learn=k_learn, plain=code_ref.outputs(per_job, dev),
+                             batched=code_t.outputs(per_job, dev)))
+    torch.cuda.synchronize()
+    out["generate_seconds"] = time.time() - t0
+    info_bits = sum(j["K"] * per_job for j in jobs)
+
+    # plain FWBF, paper setting: one launch per code and point
+    def plain():
+        for j in jobs:
+            fwbf.fwbf_decode(j["code_ref"].handle, j["q"], max_iter, 1.5, *j["plain"])
+
+    plain()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plain()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1) / reps
+
+    # learned + batched: one graph-captured launch over every code and point
+    spec = []
+    for j in jobs:
+        job = (j["code_t"].handle, j["q"], max_iter, j["a_t"], *j["batched"])
+        if j["net"] is not None:
+            job = job + (j["net"].blob, j["k_learn"])
+        spec.append(job)
+    # CTA shape tuned on 1/16 of every job's frames (the packed decoder; the
+    # list decoder gives the same results, slower)
+    sub = max(1, per_job // 16)
+    small = [(j[0], j[1][:sub], j[2], j[3], j[4][:sub], j[5][:sub]) + tuple(j[6:]) for j in spec]
+    shape, _ = autotune.tune_batch_shape(small, warps_candidates=(8, 16), packed_candidates=(1,))
+    batch = fwbf.fwbf_batch_create(spec, warps_per_cta=shape["warps_per_cta"], packed=shape["packed"])
+    s = torch.cuda.Stream()
+    try:
+        with torch.cuda.stream(s):
+            fwbf.fwbf_decode_batch(batch, s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fwbf.fwbf_decode_batch(batch, s)
+        with torch.cuda.stream(s):
+            g.replay()
+            torch.cuda.synchronize()
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(s)
+            for _ in range(reps):
+                g.replay()
+            b1.record(s)
+        torch.cuda.synchronize()
+        assert fwbf.fwbf_batch_status() == 0
+        ms_batched = b0.elapsed_time(b1) / reps
+    finally:
+        fwbf.fwbf_batch_destroy(batch)
+
+    for j in jobs:
+        row = {"code": j["key"], "ebn0_db": j["ebn0"], "frames": per_job}
+        for arm in ("plain", "batched"):
+            bits, iters = j[arm]
+            fe, be = _errors(bits, iters, j["pool_c"])
+            row[arm] = {"fer": fe / per_job, "fer_ci95": wilson(fe, per_job),
+                        "ber": be / (per_job * j["pool_c"].shape[1]),
+                        "failed_frac": float((iters < 0).float().mean().item())}
+        out["jobs"].append(row)
+    out["plain"] = {"ms": ms_plain, "gbps": info_bits / (ms_plain / 1e3) / 1e9, "launches": len(jobs)}
+    out["learned_batched"] = {"ms": ms_batched, "gbps": info_bits / (ms_batched / 1e3) / 1e9, "launches": 1,
+                              "shape": shape}
+    for code in handles:
+        code.close()
+    return out
+
+
 def main():
     import argparse
 
@@ -82,13 +242,18 @@ def main():
     import __graft_entry__
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["tab1", "eg255"])
+    ap.add_argument("what", choices=["tab1", "eg255", "scale4"])
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    res = tab1(args.frames or (1 << 16)) if args.what == "tab1" else eg255(args.frames or (1 << 17))
+    if args.what == "tab1":
+        res = tab1(args.frames or (1 << 16))
+    elif args.what == "eg255":
+        res = eg255(args.frames or (1 << 17))
+    else:
+        res = scale4(args.frames or (1 << 22))
     text = json.dumps(res, indent=1)
     if args.out:
         with open(args.out, "w") as f:

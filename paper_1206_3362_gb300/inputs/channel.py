@@ -48,7 +48,8 @@ def bpsk_awgn_torch(c, ebn0_db: float, rate: float, seed: int):
 
 def random_codewords_torch(encoder, n_frames: int, seed: int, device):
     """Seeded information bits and codewords built on the device: parity bits
-    are an exact 0/1 matrix product (sums <= K < 2^24 in fp32) reduced mod 2."""
+    are an exact 0/1 matrix product reduced mod 2 (TF32 tensor-core inputs hold
+    0 and 1 exactly and the fp32 sums stay below K < 2^24)."""
     import torch
 
     g = torch.Generator(device=device)
@@ -60,7 +61,12 @@ def random_codewords_torch(encoder, n_frames: int, seed: int, device):
     par_pos = torch.as_tensor(encoder.parity_pos, device=device)
     c[:, info] = u
     chunk = 1 << 16
-    for s0 in range(0, n_frames, chunk):
-        par = (u[s0:s0 + chunk].to(torch.float32) @ a).to(torch.int64) & 1
-        c[s0:s0 + chunk, par_pos] = par.to(torch.uint8)
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        for s0 in range(0, n_frames, chunk):
+            par = (u[s0:s0 + chunk].to(torch.float32) @ a).to(torch.int64) & 1
+            c[s0:s0 + chunk, par_pos] = par.to(torch.uint8)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
     return u, c

@@ -28,7 +28,12 @@ import numpy as np
 
 from . import fwbf
 
-DEFAULT_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "fwbf_mlp_eg1023.npz")
+WEIGHTS_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights")
+DEFAULT_WEIGHTS = os.path.join(WEIGHTS_DIR, "fwbf_mlp_eg1023.npz")
+
+
+def weights_path(code_key: str) -> str:
+    return os.path.join(WEIGHTS_DIR, f"fwbf_mlp_{code_key}.npz")
 
 
 @dataclasses.dataclass
@@ -322,9 +327,10 @@ def evaluate_batched(code, q, c, net: Network | None, sch: Schedule, max_iter: i
 
 
 def main():
-    """Config: EG(1023,781), 3.0-4.5 dB; autotune (p, alpha) at 4 dB, label and
-    train on seeded frames, evaluate plain (paper setting), tuned plain and
-    learned (batched, graph-captured) on held-out frames."""
+    """Default: EG(1023,781), 3.0-4.5 dB; autotune (p, alpha) at 4 dB, label
+    and train on seeded frames, evaluate plain (paper setting), tuned plain and
+    learned (batched, graph-captured) on held-out frames.  --code / --ebn0 /
+    --p-ref / --tune-ebn0 select another cyclic code and channel range."""
     import argparse
     import json
 
@@ -333,20 +339,25 @@ def main():
     from . import autotune
     from .inputs import Encoder, make_code
 
-    ap = argparse.ArgumentParser(description="train and evaluate the learned FWBF schedule on EG(1023,781)")
+    ap = argparse.ArgumentParser(description="train and evaluate the learned FWBF schedule on a cyclic code")
+    ap.add_argument("--code", default="eg1023")
+    ap.add_argument("--ebn0", default="3.0,3.5,4.0,4.5", help="comma-separated Eb/N0 points (dB)")
+    ap.add_argument("--p-ref", type=int, default=31, help="the paper-setting block length of the comparison")
+    ap.add_argument("--tune-ebn0", type=float, default=4.0)
     ap.add_argument("--train-frames", type=int, default=1 << 22)
     ap.add_argument("--eval-frames", type=int, default=1 << 18, help="held-out frames per Eb/N0 point")
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--k-learn", type=int, default=8)
-    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--out", default=None, help="weights file (default: weights/fwbf_mlp_<code>.npz)")
     ap.add_argument("--report", default=None)
     ap.add_argument("--weights", default=None, help="evaluate these weights instead of training")
     args = ap.parse_args()
     torch.cuda.set_device(0)
-    h = make_code("eg1023")
+    h = make_code(args.code)
     enc = Encoder(h)
-    ebn0 = (3.0, 3.5, 4.0, 4.5)
-    tune = autotune.tune_code(h, enc, 4.0, p_ref=31, alpha_ref=1.5, frames=1 << 16)
+    ebn0 = tuple(float(x) for x in args.ebn0.split(","))
+    out_path = args.out or weights_path(args.code)
+    tune = autotune.tune_code(h, enc, args.tune_ebn0, p_ref=args.p_ref, alpha_ref=1.5, frames=1 << 16)
     p_star, a_star = tune["choice"]["p"], tune["choice"]["alpha"]
     print(json.dumps({"autotune": tune["choice"], "reference": tune["reference"]}), flush=True)
     sch = Schedule(alpha_default=a_star, k_learn=args.k_learn)
@@ -362,13 +373,14 @@ def main():
     else:
         net, summary = train_pipeline(code, enc, args.train_frames, ebn0, sch, epochs=args.epochs,
                                       log=lambda m: print(m, flush=True))
-        net.save(args.out, seg_len=p_star, k_learn=sch.k_learn, alpha_default=sch.alpha_default)
-    res = {"autotune": tune, "train": summary, "seg_len": p_star, "alpha": a_star, "k_learn": sch.k_learn}
+        net.save(out_path, seg_len=p_star, k_learn=sch.k_learn, alpha_default=sch.alpha_default)
+    res = {"code": args.code, "autotune": tune, "train": summary, "seg_len": p_star, "alpha": a_star,
+           "k_learn": sch.k_learn}
     paper = Schedule(alpha_default=1.5, k_learn=sch.k_learn)
-    code31 = fwbf.Code.from_parity_check(h, 31)
+    code31 = fwbf.Code.from_parity_check(h, args.p_ref)
     for eb in ebn0:
         q, c = make_frames(code, enc, args.eval_frames, (eb,), seed=777, device="cuda")
-        res[f"{eb}dB"] = {"plain_p31": evaluate(code31, q, c, None, paper),
+        res[f"{eb}dB"] = {f"plain_p{args.p_ref}": evaluate(code31, q, c, None, paper),
                           "plain_tuned": evaluate(code, q, c, None, sch),
                           "learned_batched": evaluate_batched(code, q, c, net, sch)}
         print(json.dumps({f"{eb}dB": res[f"{eb}dB"]}), flush=True)

@@ -30,8 +30,9 @@ def test_tune_code_eg1023(fwbf, tmp_path):
     ref = res["reference"]
     ch = res["choice"]
     chosen = [r for r in res["candidates"] if r["p"] == ch["p"] and r["alpha"] == ch["alpha"]][0]
-    assert chosen["frame_errors"] <= ref["frame_errors"]
-    qualified = [r for r in res["candidates"] if r["frame_errors"] <= ref["frame_errors"]]
+    assert chosen["frame_errors"] <= ref["frame_errors"] and chosen["bit_errors"] <= ref["bit_errors"]
+    qualified = [r for r in res["candidates"]
+                 if r["frame_errors"] <= ref["frame_errors"] and r["bit_errors"] <= ref["bit_errors"]]
     assert chosen["ms"] == min(r["ms"] for r in qualified)
     print("autotune eg1023 4 dB:", res["choice"], "ref", ref, "chosen", chosen)
     again = autotune.Cache(str(tmp_path / "c.json")).get(cache.key(h, 4.0))

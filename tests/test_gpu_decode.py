@@ -109,6 +109,23 @@ def test_other_codes(fwbf, key, p):
     assert_same(fwbf, h, p, oracle.quantize(y), 30, 1.5)
 
 
+def test_generic_kernel_warp_groups(fwbf):
+    """Codes whose frames fill a block's shared memory run several warps per
+    frame in the list decoder: QC N = 16384 (8 warps, wide rows: a check's
+    edges shared by the lanes) and a random (3,6) N = 8064 code (narrow rows:
+    a lane per syndrome word), both against the oracle, with a ragged tail."""
+    from paper_1206_3362_gb300.inputs.codes import random_regular
+
+    h, c, y = frames("qc16384", 37, 5.5, seed=61)
+    with fwbf.Code.from_parity_check(h, 32) as code:
+        assert code.info.Z == 512
+    assert_same(fwbf, h, 32, oracle.quantize(y), 30, 1.5)
+    h = random_regular(8064, 3, 6, seed=62)
+    enc = Encoder(h)
+    _, c = random_codewords(enc, 45, seed=63)
+    assert_same(fwbf, h, 32, oracle.quantize(bpsk_awgn(c, 6.0, enc.rate, seed=63)), 40, 1.0)
+
+
 def test_generic_kernel_on_permuted_eg1023(fwbf):
     """The same EG(1023,781) code with its columns permuted has no circulant
     structure, so it runs through the generic (list-based) kernel instead of

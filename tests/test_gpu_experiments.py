@@ -44,3 +44,20 @@ def test_eg255_kmax5_vs_10(built):
     for row in res["rows"].values():
         assert row["p16_kmax10"]["fer"] <= row["p16_kmax5"]["fer"]
         assert row["p16_kmax5"]["ber"] <= 2.0 * row["p16_kmax10"]["ber"] + 1e-6
+
+
+def test_scale4_small(built):
+    """Learned + batched at scale, on 512 frames per code and point: the
+    rate-0.94 column-weight-4 QC code is beyond bit flipping at 4 dB in both
+    arms, EG(4095,3367) decodes at 5.5 dB in both."""
+    from paper_1206_3362_gb300 import experiments
+
+    out = experiments.scale4(frames=8 * 512, reps=1)
+    assert out["frames_per_job"] == 512 and len(out["jobs"]) == 8
+    assert out["plain"]["launches"] == 8 and out["learned_batched"]["launches"] == 1
+    rows = {(r["code"], r["ebn0_db"]): r for r in out["jobs"]}
+    for arm in ("plain", "batched"):
+        assert rows[("qc16384", 4.0)][arm]["fer"] >= 0.9
+        assert rows[("eg4095", 5.5)][arm]["fer"] <= 0.01
+        for r in out["jobs"]:
+            assert 0.0 <= r[arm]["ber"] <= r[arm]["fer"] <= 1.0

@@ -139,23 +139,30 @@ def test_features_match_oracle_trace(fwbf):
 # learned schedule
 # ---------------------------------------------------------------------------
 
-def test_decode_learned_replays_exactly(fwbf):
-    """The (alpha_q, theta_q) the network chose are recorded; the oracle run
-    with that schedule reproduces every frame solved in the learned passes, and
-    plain FWBF reproduces every frame handed to the fallback."""
+def _varied_network():
     from paper_1206_3362_gb300.learned import Network
 
-    h, c, q = frames("eg1023", 300, 3.25, seed=44)
-    k_learn, K = 6, 60
     net = Network(seed=7)
     m = net.master.cpu().numpy()
     rng = np.random.default_rng(8)
     m[4608:4736] = rng.standard_normal(128) * 0.3   # W3: outputs vary with the features
     m[4864:4866] = [1.5, 0.15]
     net.set_master(m)
-    with fwbf.Code.from_parity_check(h, 8) as code:
-        bits, iters = code.outputs(300)
-        sched = torch.full((300, k_learn, 2), -1, dtype=torch.int32, device="cuda")
+    return net
+
+
+# eg1023 runs two warps per frame, eg4095 four
+@pytest.mark.parametrize("key,p,F,ebn0", [("eg1023", 8, 300, 3.25), ("eg4095", 64, 96, 3.75)])
+def test_decode_learned_replays_exactly(fwbf, key, p, F, ebn0):
+    """The (alpha_q, theta_q) the network chose are recorded; the oracle run
+    with that schedule reproduces every frame solved in the learned passes, and
+    plain FWBF reproduces every frame handed to the fallback."""
+    h, c, q = frames(key, F, ebn0, seed=44)
+    k_learn, K = 6, 60
+    net = _varied_network()
+    with fwbf.Code.from_parity_check(h, p) as code:
+        bits, iters = code.outputs(F)
+        sched = torch.full((F, k_learn, 2), -1, dtype=torch.int32, device="cuda")
         fwbf.fwbf_decode_learned(code.handle, torch.from_numpy(q).cuda(), K, k_learn, 1.5, net.blob, bits, iters,
                                  out_sched=sched)
         torch.cuda.synchronize()
@@ -164,16 +171,49 @@ def test_decode_learned_replays_exactly(fwbf):
     s = sched.cpu().numpy()
     assert len(np.unique(s[:, 0, 0])) > 3  # the network really varies alpha
     learned = (it >= 0) & (it <= k_learn)
-    A = np.full((300, K), 384, dtype=np.int32)
-    T = np.zeros((300, K), dtype=np.int32)
+    A = np.full((F, K), 384, dtype=np.int32)
+    T = np.zeros((F, K), dtype=np.int32)
     A[:, :k_learn] = np.where(s[:, :, 0] >= 0, s[:, :, 0], 384)
     T[:, :k_learn] = np.where(s[:, :, 1] >= 0, s[:, :, 1], 0)
-    bo, io = oracle.fwbf_i8(h, 8, q[learned], K, alpha_sched=A[learned], theta_sched=T[learned])
+    bo, io = oracle.fwbf_i8(h, p, q[learned], K, alpha_sched=A[learned], theta_sched=T[learned])
     assert np.array_equal(io, it[learned]) and np.array_equal(bo, b[learned])
     fb = ~learned
-    bp, ip = oracle.fwbf_i8(h, 8, q[fb], K, alpha=1.5)
+    bp, ip = oracle.fwbf_i8(h, p, q[fb], K, alpha=1.5)
     assert np.array_equal(bp, b[fb])
     assert np.array_equal(np.where(ip >= 0, ip + k_learn, ip), it[fb])
+
+
+def test_batched_learned_job_equals_single_code(fwbf):
+    """A learned EG(4095) job (four warps per frame in the batch) beside a plain
+    EG(1023) job gives exactly the single-code learned and plain results."""
+    net = _varied_network()
+    specs, singles, codes = [], [], []
+    try:
+        for key, p, F, learned in (("eg4095", 64, 150, True), ("eg1023", 31, 400, False)):
+            h, c, q = frames(key, F, 3.75, seed=45)
+            code = fwbf.Code.from_parity_check(h, p)
+            codes.append(code)
+            qd = torch.from_numpy(q).cuda()
+            b1, i1 = code.outputs(F)
+            if learned:
+                fwbf.fwbf_decode_learned(code.handle, qd, 60, 4, 1.5, net.blob, b1, i1)
+            else:
+                fwbf.fwbf_decode(code.handle, qd, 60, 1.5, b1, i1)
+            b2, i2 = code.outputs(F)
+            specs.append((code.handle, qd, 60, 1.5, b2, i2) + ((net.blob, 4) if learned else ()))
+            singles.append((b1, i1, b2, i2))
+        batch = fwbf.fwbf_batch_create(specs, warps_per_cta=16, packed=1)
+        try:
+            fwbf.fwbf_decode_batch(batch)
+            torch.cuda.synchronize()
+            assert fwbf.fwbf_batch_status() == 0
+        finally:
+            fwbf.fwbf_batch_destroy(batch)
+        for b1, i1, b2, i2 in singles:
+            assert torch.equal(i1, i2) and torch.equal(b1, b2)
+    finally:
+        for code in codes:
+            code.close()
 
 
 def test_trained_network_gain(fwbf):
