@@ -123,6 +123,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
     int *red = reinterpret_cast<int *>(ws + P.off_red);
+    float *mlp_slot = reinterpret_cast<float *>(ws + P.off_red + 128);  // network halves (WPF > 1)
     int rhalf = 0;
     const int Z = P.Z, H = P.H, DC = P.DC;
     const int Zw = (Z + 31) >> 5;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                 tq = P.sched_t[o];
             } else if (mode == kModeLearned) {
                 float al, th;
-                mlp_eval(P.mlp, feat, lane, al, th);  // every warp of the group: identical results
+                mlp_eval<WPF>(P.mlp, feat, lane, gw, mlp_slot, bar_id, al, th);
                 th *= 16.0f;
                 aq = __float2int_rn(fminf(fmaxf(al, 0.0f), 64.0f) * 256.0f);
                 tq = __float2int_rn(fminf(fmaxf(th, 0.0f), 4096.0f) * 256.0f);
@@ -438,8 +439,8 @@ inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
     o += a16(4 * ((Z + 31) / 32));
     P.off_keys = o;
     o += a16(8 * (uint32_t)c->B);
-    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 4 warps
-    o += 128;
+    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 4 warps; then 4 floats for the network
+    o += 144;
     P.warp_bytes = o;
     P.table_smem_bytes = a16(c->table_words * 4u);
 }

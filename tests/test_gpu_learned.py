@@ -184,12 +184,15 @@ def test_decode_learned_replays_exactly(fwbf, key, p, F, ebn0):
 
 
 def test_batched_learned_job_equals_single_code(fwbf):
-    """A learned EG(4095) job (four warps per frame in the batch) beside a plain
-    EG(1023) job gives exactly the single-code learned and plain results."""
+    """A learned EG(4095) job (four warps per frame in the batch and alone), a
+    learned EG(1023) job (one warp per frame in the batch, two alone) and a
+    plain EG(1023) job give exactly the single-code results: the network's
+    arithmetic order does not depend on how many warps evaluate it."""
     net = _varied_network()
     specs, singles, codes = [], [], []
     try:
-        for key, p, F, learned in (("eg4095", 64, 150, True), ("eg1023", 31, 400, False)):
+        for key, p, F, learned in (("eg4095", 64, 150, True), ("eg1023", 16, 400, True),
+                                   ("eg1023", 31, 400, False)):
             h, c, q = frames(key, F, 3.75, seed=45)
             code = fwbf.Code.from_parity_check(h, p)
             codes.append(code)
