@@ -38,7 +38,7 @@ WORKLOAD = dict(code="eg1023", ebn0_db=4.0, frames=1 << 20, max_iter=100, seg_le
 # (fwbf_decode_i8_cyclic_kernel<8, 2>, 131,072 frames of this workload; scaled by
 # frames, since traffic is the frame bytes in and the decisions out); see
 # profiles/fwbf_decode_i8_eg1023_4dB.md.  Set to None when the kernel changes.
-DECODE_TRAFFIC_BYTES_PER_FRAME = (134.258688e6 + 8.962048e6) / 131072
+DECODE_TRAFFIC_BYTES_PER_FRAME = (134.153472e6 + 8.916480e6) / 131072
 DECODE_KERNEL = "fwbf_decode_i8_cyclic_kernel<8, 2>"
 
 
