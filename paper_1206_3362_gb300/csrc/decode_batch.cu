@@ -27,7 +27,7 @@ namespace fwbf {
 __device__ int g_status_batch;
 
 enum JobKind : int { kJobGenericPlain = 0, kJobGenericCirc = 1, kJobCyclic4 = 2, kJobCyclic8 = 3, kJobCyclic2 = 4,
-                     kJobCyclic1 = 5, kJobCyclic8W2 = 6, kJobCyclic8W4 = 7 };
+                     kJobCyclic1 = 5, kJobCyclic4W2 = 6, kJobCyclic8W4 = 7 };
 
 struct BatchJob {
     int kind;
@@ -43,9 +43,10 @@ struct BatchJob {
 
 constexpr int kMaxJobs = 16;
 
-// The CTA's frames of a cyclic job decoded by groups of WPF warps (group g
-// meets at named barrier 1 + g; the CTA-wide barrier 0 is not used meanwhile).
-template <int WPF>
+// The CTA's frames of a cyclic job decoded by groups of WPF warps, R pairs
+// per lane per chunk (group g meets at named barrier 1 + g; the CTA-wide
+// barrier 0 is not used meanwhile).
+template <int R, int WPF>
 __device__ __forceinline__ void batch_cyclic_groups(const BatchJob &J, const uint32_t *d_off, const uint32_t *u_off,
                                                     unsigned char *smem, unsigned long long *fslot) {
     constexpr int G = 32 * WPF;
@@ -58,7 +59,7 @@ __device__ __forceinline__ void batch_cyclic_groups(const BatchJob &J, const uin
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];
         if (f >= (unsigned long long)J.F) break;
-        cyclic_frame<8, WPF>(J.cp, d_off, u_off, ws, t, bar_id, f);
+        cyclic_frame<R, WPF>(J.cp, d_off, u_off, ws, t, bar_id, f);
     }
 }
 
@@ -128,10 +129,10 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
         }
         __syncthreads();
         if (warp < J.warps && J.wpf > 1) {
-            if (J.kind == kJobCyclic8W2)
-                batch_cyclic_groups<2>(J, d_off, u_off, smem, fslot);
+            if (J.kind == kJobCyclic4W2)
+                batch_cyclic_groups<4, 2>(J, d_off, u_off, smem, fslot);
             else if (J.kind == kJobCyclic8W4)
-                batch_cyclic_groups<4>(J, d_off, u_off, smem, fslot);
+                batch_cyclic_groups<8, 4>(J, d_off, u_off, smem, fslot);
             else if (J.kind == kJobGenericPlain)
                 batch_generic_dispatch<true>(J, st, smem, fslot);
             else
@@ -246,12 +247,14 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         int frames = (int)(((uint32_t)optin - reserve - b.table_smem_bytes) / b.warp_bytes);
         if (frames > warps_per_cta) frames = warps_per_cta;
         // codes whose frames fill the shared memory before the warps run out:
-        // 2 or 4 warps per frame (packed R = 8 decoder), 2, 4 or 8 (list decoder)
+        // 4 warps per frame (packed decoder, R = 8) or 2 (R = 4) when H / 32
+        // gives every warp a chunk; 2, 4 or 8 (list decoder)
         b.wpf = 1;
         const int spare = warps_per_cta / frames;
-        if (b.kind == kJobCyclic8) {
-            b.wpf = spare >= 4 ? 4 : spare >= 2 ? 2 : 1;
-            if (b.wpf > 1) b.kind = b.wpf == 4 ? kJobCyclic8W4 : kJobCyclic8W2;
+        if (b.kind >= kJobCyclic4) {
+            const int ppl = b.cp.H / 32;
+            b.wpf = spare >= 4 && ppl % 8 == 0 && ppl / 8 >= 4 ? 4 : spare >= 2 && ppl % 4 == 0 && ppl / 4 >= 2 ? 2 : 1;
+            if (b.wpf > 1) b.kind = b.wpf == 4 ? kJobCyclic8W4 : kJobCyclic4W2;
         } else if (b.kind <= kJobGenericCirc) {
             b.wpf = spare >= 8 ? 8 : spare >= 4 ? 4 : spare >= 2 ? 2 : 1;
         }
