@@ -59,7 +59,10 @@ __device__ __forceinline__ void batch_cyclic_groups(const BatchJob &J, const uin
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];
         if (f >= (unsigned long long)J.F) break;
-        cyclic_frame<R, WPF>(J.cp, d_off, u_off, ws, t, bar_id, f);
+        if (J.cp.mode == kModePlain)
+            cyclic_frame<R, WPF, true>(J.cp, d_off, u_off, ws, t, bar_id, f);
+        else
+            cyclic_frame<R, WPF, false>(J.cp, d_off, u_off, ws, t, bar_id, f);
     }
 }
 
@@ -79,6 +82,16 @@ __device__ __forceinline__ void batch_generic_groups(const BatchJob &J, const ui
         if (f >= (unsigned long long)J.F) break;
         generic_frame<PLAIN, WPF>(J.gp, tbl, ws, t, bar_id, f);
     }
+}
+
+// One frame of a cyclic job by one warp (plain jobs run the plain-only body).
+template <int R>
+__device__ __forceinline__ void cyclic_frame_job(const BatchJob &J, const uint32_t *d_off, const uint32_t *u_off,
+                                                 unsigned char *ws, int lane, unsigned long long f) {
+    if (J.cp.mode == kModePlain)
+        cyclic_frame<R, 1, true>(J.cp, d_off, u_off, ws, lane, 0, f);
+    else
+        cyclic_frame<R, 1, false>(J.cp, d_off, u_off, ws, lane, 0, f);
 }
 
 template <bool PLAIN>
@@ -152,10 +165,10 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
                 switch (J.kind) {
                     case kJobGenericPlain: generic_frame<true, 1>(J.gp, st, ws, lane, 0, f); break;
                     case kJobGenericCirc: generic_frame<false, 1>(J.gp, st, ws, lane, 0, f); break;
-                    case kJobCyclic8: cyclic_frame<8, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
-                    case kJobCyclic4: cyclic_frame<4, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
-                    case kJobCyclic2: cyclic_frame<2, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
-                    default: cyclic_frame<1, 1>(J.cp, d_off, u_off, ws, lane, 0, f); break;
+                    case kJobCyclic8: cyclic_frame_job<8>(J, d_off, u_off, ws, lane, f); break;
+                    case kJobCyclic4: cyclic_frame_job<4>(J, d_off, u_off, ws, lane, f); break;
+                    case kJobCyclic2: cyclic_frame_job<2>(J, d_off, u_off, ws, lane, f); break;
+                    default: cyclic_frame_job<1>(J, d_off, u_off, ws, lane, f); break;
                 }
             }
         }

@@ -34,7 +34,7 @@ namespace fwbf {
 
 __device__ int g_status_i8_cyclic;
 
-template <int R, int WPF>  // pairs per lane per chunk, warps per frame
+template <int R, int WPF, bool PLAIN_ONLY>  // pairs per lane per chunk, warps per frame, plain FWBF alone
 __global__ void __launch_bounds__(512, WPF == 2 ? 2 : 1) fwbf_decode_i8_cyclic_kernel(const CyclicParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(512, WPF == 2 ? 2 : 1) fwbf_decode_i8_cyclic_k
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];  // rewritten only after the frame's last meeting
         if (f >= (unsigned long long)P.F) break;
-        cyclic_frame<R, WPF>(P, d_off, u_off, ws, t, bar_id, f);
+        cyclic_frame<R, WPF, PLAIN_ONLY>(P, d_off, u_off, ws, t, bar_id, f);
     }
 }
 
@@ -131,13 +131,20 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     const int wpf = fmax >= 8 ? 2 : 4;
     int frames = wpf == 2 ? (fmax >= 16 ? 8 : fmax / 2) : (fmax < 4 ? fmax : 4);
     const int R = cyclic_R(c, wpf);
+    const bool plain = P.mode == kModePlain && !P.out_feat;
     void (*kern)(const CyclicParams);
-    if (wpf == 2)
-        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 2> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 2>
-             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 2> : fwbf_decode_i8_cyclic_kernel<1, 2>;
+    if (wpf == 2 && plain)
+        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 2, true> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 2, true>
+             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 2, true> : fwbf_decode_i8_cyclic_kernel<1, 2, true>;
+    else if (wpf == 2)
+        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 2, false> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 2, false>
+             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 2, false> : fwbf_decode_i8_cyclic_kernel<1, 2, false>;
+    else if (plain)
+        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 4, true> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 4, true>
+             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 4, true> : fwbf_decode_i8_cyclic_kernel<1, 4, true>;
     else
-        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 4> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 4>
-             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 4> : fwbf_decode_i8_cyclic_kernel<1, 4>;
+        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 4, false> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 4, false>
+             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 4, false> : fwbf_decode_i8_cyclic_kernel<1, 4, false>;
     int per_sm = 0;
     uint32_t dyn = 0;
     cudaError_t e = cudaSuccess;
