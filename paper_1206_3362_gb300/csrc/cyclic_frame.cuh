@@ -333,7 +333,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                 uint32_t cmask = (G2 + SC2 + dfilter) & 0x80008000u;
                 if (i + H >= Z) cmask &= 0x8000u;  // the duplicated position
                 if (cmask == 0u) continue;
-                ncand += __popc(cmask);
+                if (!PLAIN_ONLY) ncand += __popc(cmask);  // a feature of the next pass
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     const int n = i + half * H;
