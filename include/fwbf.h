@@ -200,16 +200,22 @@ typedef struct {
     uint32_t *out_bits;    /* device uint32 [n_frames][ceil(N/32)] */
     int32_t *out_iters;    /* device int32 [n_frames] */
     const void *mlp;       /* NULL: plain FWBF; else the learned network (see
-                              fwbf_decode_learned), cyclic codes with packed = 1 only */
+                              fwbf_decode_learned), cyclic codes with packed = 1 or 2 */
     int32_t k_learn;       /* learned passes before the plain fallback (mlp != NULL) */
 } fwbf_batch_job;
 
 /*
  * Builds a batch of 1..16 jobs (the descriptors are copied; buffers must stay
  * valid while the batch is used).
- *   warps_per_cta   1..16: warps (one frame each) per CTA of the launch
+ *   warps_per_cta   1..16: warps per CTA of the launch (packed = 0 or 1)
  *   packed          1: cyclic codes use the packed two-positions-per-register
- *                   decoder; 0: every code uses the list decoder
+ *                   decoder; 0: every code uses the list decoder; 2: as 1,
+ *                   with every frame decoded by a group of 2 or 4 warps in two
+ *                   512-thread CTAs per SM when every job allows it (cyclic
+ *                   codes with H / 32 divisible by 4 and at least 8; any code
+ *                   of the list decoder), else as 1 (warps_per_cta is then
+ *                   ignored when the grouped launch is taken).  Results are the
+ *                   same for every choice.
  * Allocates the device job table and one frame counter per job (owned by the
  * handle).  Errors: FWBF_EINVAL, FWBF_EUNSUPPORTED (a code too large for one
  * warp's shared memory), FWBF_ENOMEM, FWBF_ECUDA.

@@ -9,7 +9,8 @@ Tuned per code, on seeded calibration frames at a chosen Eb/N0:
   p and alpha);
 * the decoder variant ("bit-packing width": the packed cyclic decoder with two
   positions per 32-bit register, or the list decoder with one), and, for a
-  batch, the number of warps (frames in flight) per CTA.
+  batch, the number of warps per CTA and whether every frame is decoded by a
+  group of warps ("lanes per frame": packed = 2).
 
 Among admitted settings the fastest (CUDA-event time of the decode) wins.
 Results are cached in a JSON file keyed by code, Eb/N0 and GPU name.
@@ -100,13 +101,14 @@ def tune_code(h, enc, ebn0: float, p_ref: int, alpha_ref: float = 1.5, frames: i
             "frames": frames, "ebn0_db": ebn0}
 
 
-def tune_batch_shape(jobs, warps_candidates=(4, 8, 12, 16), packed_candidates=(1, 0)):
+def tune_batch_shape(jobs, warps_candidates=(4, 8, 12, 16), packed_candidates=(2, 1, 0)):
     """Fastest (warps_per_cta, packed) for a batch of jobs [(code, y, max_iter,
-    alpha, bits, iters)]; both variants give identical results."""
+    alpha, bits, iters)]; every variant gives identical results.  packed = 2
+    (warp groups, fixed 512-thread CTAs) is timed once, at 16 warps."""
     best = None
     rows = []
     for packed in packed_candidates:
-        for w in warps_candidates:
+        for w in ((16,) if packed == 2 else warps_candidates):
             b = fwbf.fwbf_batch_create(jobs, warps_per_cta=w, packed=packed)
             try:
                 ms = _time(lambda: fwbf.fwbf_decode_batch(b))

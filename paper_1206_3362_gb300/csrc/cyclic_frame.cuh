@@ -125,7 +125,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
     int *red = reinterpret_cast<int *>(ws + P.off_red);
-    float *mlp_slot = reinterpret_cast<float *>(ws + P.off_red + 128);  // network halves (WPF > 1)
+    float *mlp_slot = reinterpret_cast<float *>(ws + P.off_red + 32 * WPF);  // network halves (WPF > 1)
     int rhalf = 0;
     const int Z = P.Z, H = P.H, DC = P.DC;
     const int Zw = (Z + 31) >> 5;
@@ -415,6 +415,12 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
 bool cyclic_eligible(const fwbf_code_s *c);
 
 // Host: fills the code-dependent fields and the per-warp shared-memory layout.
+// bytes of a frame's group scratch for wpf warps (the last item of the slice)
+inline uint32_t cyclic_red_bytes(int wpf) { return (32u * (uint32_t)wpf + 16u + 15u) & ~15u; }
+
+// Sizes the frame's slice for groups of wpf warps (cyclic_layout assumes 4).
+inline void cyclic_set_wpf(CyclicParams &P, int wpf) { P.warp_bytes = P.off_red + cyclic_red_bytes(wpf); }
+
 inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
     auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
     P.table = c->d_table;
@@ -441,9 +447,8 @@ inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
     o += a16(4 * ((Z + 31) / 32));
     P.off_keys = o;
     o += a16(8 * (uint32_t)c->B);
-    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 4 warps; then 4 floats for the network
-    o += 144;
-    P.warp_bytes = o;
+    P.off_red = o;  // group sums: 2 halves x 4 ints per warp of the group; then 4 floats for the network
+    P.warp_bytes = o + cyclic_red_bytes(4);
     P.table_smem_bytes = a16(c->table_words * 4u);
 }
 

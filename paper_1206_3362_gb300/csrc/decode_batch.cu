@@ -27,7 +27,7 @@ namespace fwbf {
 __device__ int g_status_batch;
 
 enum JobKind : int { kJobGenericPlain = 0, kJobGenericCirc = 1, kJobCyclic4 = 2, kJobCyclic8 = 3, kJobCyclic2 = 4,
-                     kJobCyclic1 = 5, kJobCyclic4W2 = 6, kJobCyclic8W4 = 7 };
+                     kJobCyclic1 = 5, kJobCyclic4W2 = 6, kJobCyclic8W4 = 7, kJobCyclic4W4 = 8 };
 
 struct BatchJob {
     int kind;
@@ -105,7 +105,11 @@ __device__ __forceinline__ void batch_generic_dispatch(const BatchJob &J, const 
         batch_generic_groups<PLAIN, 8>(J, tbl, smem, fslot);
 }
 
-__global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJob *__restrict__ jobs, int n_jobs) {
+// GROUPED: every job runs warp groups (two blocks of 512 threads per SM, 64
+// registers); otherwise any mix of one-warp and group jobs (one block per SM).
+template <bool GROUPED>
+__global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel(const BatchJob *__restrict__ jobs,
+                                                                                  int n_jobs) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bars[kMaxJobs];
     __shared__ int flag;
@@ -142,15 +146,19 @@ __global__ void __launch_bounds__(512, 1) fwbf_decode_batch_kernel(const BatchJo
         }
         __syncthreads();
         if (warp < J.warps && J.wpf > 1) {
-            if (J.kind == kJobCyclic4W2)
+            if (J.kind == kJobCyclic4W2) {
                 batch_cyclic_groups<4, 2>(J, d_off, u_off, smem, fslot);
-            else if (J.kind == kJobCyclic8W4)
-                batch_cyclic_groups<8, 4>(J, d_off, u_off, smem, fslot);
-            else if (J.kind == kJobGenericPlain)
+            } else if (J.kind == kJobCyclic8W4 || J.kind == kJobCyclic4W4) {
+                if constexpr (GROUPED)
+                    batch_cyclic_groups<4, 4>(J, d_off, u_off, smem, fslot);
+                else
+                    batch_cyclic_groups<8, 4>(J, d_off, u_off, smem, fslot);
+            } else if (J.kind == kJobGenericPlain) {
                 batch_generic_dispatch<true>(J, st, smem, fslot);
-            else
+            } else {
                 batch_generic_dispatch<false>(J, st, smem, fslot);
-        } else if (warp < J.warps) {
+            }
+        } else if (!GROUPED && warp < J.warps) {
             unsigned char *ws = smem + J.table_smem_bytes + warp * J.warp_bytes;
             const int B = J.kind <= kJobGenericCirc ? J.gp.nkeys : J.cp.B;
             const uint32_t off_keys = J.kind <= kJobGenericCirc ? J.gp.off_keys : J.cp.off_keys;
@@ -182,6 +190,7 @@ using namespace fwbf;
 
 struct fwbf_batch_s {
     int n_jobs = 0;
+    bool grouped = false;
     BatchJob *d_jobs = nullptr;
     unsigned long long *d_counters = nullptr;
     int blocks = 0, threads = 0;
@@ -197,6 +206,7 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
     *out = nullptr;
     if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs) return fail(FWBF_EINVAL, "n_jobs must be in [1, 16]");
     if (warps_per_cta < 1 || warps_per_cta > 16) return fail(FWBF_EINVAL, "warps_per_cta must be in [1, 16]");
+    if (packed < 0 || packed > 2) return fail(FWBF_EINVAL, "packed must be 0, 1 or 2");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -268,6 +278,8 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
             const int ppl = b.cp.H / 32;
             b.wpf = spare >= 4 && ppl % 8 == 0 && ppl / 8 >= 4 ? 4 : spare >= 2 && ppl % 4 == 0 && ppl / 4 >= 2 ? 2 : 1;
             if (b.wpf > 1) b.kind = b.wpf == 4 ? kJobCyclic8W4 : kJobCyclic4W2;
+            cyclic_set_wpf(b.cp, b.wpf);  // (frames were counted with the largest scratch)
+            b.warp_bytes = b.cp.warp_bytes;
         } else if (b.kind <= kJobGenericCirc) {
             b.wpf = spare >= 8 ? 8 : spare >= 4 ? 4 : spare >= 2 ? 2 : 1;
         }
@@ -275,11 +287,67 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         const uint32_t need = b.table_smem_bytes + frames * b.warp_bytes;
         if (need > dyn) dyn = need;
     }
+    // packed = 2: the grouped kernel (two 512-thread blocks per SM) when every
+    // job can run warp groups in half an SM's shared memory: up to 8 frames per
+    // block, two warps per frame (four when at most 4 frames fit, R = 4) for
+    // the packed decoder, 2, 4 or 8 for the list decoder
+    bool grouped = false;
+    if (packed == 2) {
+        int smem_sm = 0;
+        cudaFuncAttributes fa{};
+        e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fwbf_decode_batch_kernel<true>);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped batch query");
+        const int64_t half = (int64_t)smem_sm / 2 - 1024 - (int64_t)fa.sharedSizeBytes;
+        std::vector<BatchJob> gj = hj;
+        uint32_t gdyn = 0;
+        grouped = true;
+        for (int j = 0; j < n_jobs && grouped; ++j) {
+            BatchJob &b = gj[j];
+            const int64_t avail = half - (int64_t)b.table_smem_bytes;
+            int frames = avail > 0 ? (int)(avail / b.warp_bytes) : 0;
+            if (frames > 8) frames = 8;
+            if (frames < 1) {
+                grouped = false;
+                break;
+            }
+            if (b.kind <= kJobGenericCirc) {
+                int w = 2;
+                while (w < 8 && frames * w * 2 <= 16) w *= 2;
+                b.wpf = w;
+            } else {
+                const int ppl = b.cp.H / 32;
+                if (ppl % 4 != 0 || ppl / 4 < 2) {
+                    grouped = false;
+                    break;
+                }
+                if (frames <= 4 && ppl / 4 >= 4) {
+                    b.wpf = 4;
+                    b.kind = kJobCyclic4W4;
+                } else {
+                    b.wpf = 2;
+                    b.kind = kJobCyclic4W2;
+                }
+                cyclic_set_wpf(b.cp, b.wpf);  // the slice shrinks to the group's scratch
+                b.warp_bytes = b.cp.warp_bytes;
+                frames = (int)(avail / b.warp_bytes);
+                if (frames > (b.wpf == 4 ? 4 : 8)) frames = b.wpf == 4 ? 4 : 8;
+            }
+            b.warps = frames * b.wpf;
+            const uint32_t need = b.table_smem_bytes + frames * b.warp_bytes;
+            if (need > gdyn) gdyn = need;
+        }
+        if (grouped) {
+            hj = gj;
+            dyn = gdyn;
+        }
+    }
     fwbf_batch_s *bh = new (std::nothrow) fwbf_batch_s();
     if (!bh) return fail(FWBF_ENOMEM, "host allocation");
     bh->n_jobs = n_jobs;
     bh->device = dev;
-    bh->threads = 32 * warps_per_cta;
+    bh->grouped = grouped;
+    bh->threads = grouped ? 512 : 32 * warps_per_cta;
     bh->dyn = dyn;
     e = cudaMalloc(reinterpret_cast<void **>(&bh->d_counters), sizeof(unsigned long long) * n_jobs);
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&bh->d_jobs), sizeof(BatchJob) * n_jobs);
@@ -294,11 +362,10 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         hj[j].cp.counter = hj[j].counter;
     }
     e = cudaMemcpy(bh->d_jobs, hj.data(), sizeof(BatchJob) * n_jobs, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(fwbf_decode_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    void (*kern)(const BatchJob *, int) = grouped ? fwbf_decode_batch_kernel<true> : fwbf_decode_batch_kernel<false>;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int per_sm = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwbf_decode_batch_kernel, bh->threads, dyn);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bh->threads, dyn);
     if (e != cudaSuccess || per_sm < 1) {
         cudaFree(bh->d_counters);
         cudaFree(bh->d_jobs);
@@ -315,7 +382,10 @@ int fwbf_decode_batch(fwbf_batch b, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * b->n_jobs, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counters)");
-    fwbf_decode_batch_kernel<<<b->blocks, b->threads, b->dyn, s>>>(b->d_jobs, b->n_jobs);
+    if (b->grouped)
+        fwbf_decode_batch_kernel<true><<<b->blocks, b->threads, b->dyn, s>>>(b->d_jobs, b->n_jobs);
+    else
+        fwbf_decode_batch_kernel<false><<<b->blocks, b->threads, b->dyn, s>>>(b->d_jobs, b->n_jobs);
     e = cudaGetLastError();
     return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "decode_batch launch");
 }

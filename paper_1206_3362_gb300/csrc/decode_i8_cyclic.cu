@@ -129,6 +129,7 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     // otherwise one block and four warps per frame
     const int fmax = (int)((optin - reserve - P.table_smem_bytes) / P.warp_bytes);
     const int wpf = fmax >= 8 ? 2 : 4;
+    cyclic_set_wpf(P, wpf);
     int frames = wpf == 2 ? (fmax >= 16 ? 8 : fmax / 2) : (fmax < 4 ? fmax : 4);
     const int R = cyclic_R(c, wpf);
     const bool plain = P.mode == kModePlain && !P.out_feat;

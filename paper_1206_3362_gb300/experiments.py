@@ -189,11 +189,11 @@ def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, ma
         if j["net"] is not None:
             job = job + (j["net"].blob, j["k_learn"])
         spec.append(job)
-    # CTA shape tuned on 1/16 of every job's frames (the packed decoder; the
-    # list decoder gives the same results, slower)
+    # CTA shape tuned on 1/16 of every job's frames (the packed decoder with and
+    # without warp groups; the list decoder gives the same results, slower)
     sub = max(1, per_job // 16)
     small = [(j[0], j[1][:sub], j[2], j[3], j[4][:sub], j[5][:sub]) + tuple(j[6:]) for j in spec]
-    shape, _ = autotune.tune_batch_shape(small, warps_candidates=(8, 16), packed_candidates=(1,))
+    shape, _ = autotune.tune_batch_shape(small, warps_candidates=(8, 16), packed_candidates=(2, 1))
     batch = fwbf.fwbf_batch_create(spec, warps_per_cta=shape["warps_per_cta"], packed=shape["packed"])
     s = torch.cuda.Stream()
     try:

@@ -296,7 +296,7 @@ def evaluate_batched(code, q, c, net: Network | None, sch: Schedule, max_iter: i
     job = (code.handle, q, max_iter, sch.alpha_default, bits, iters)
     if net is not None:
         job = job + (net.blob, sch.k_learn)
-    batch = fwbf.fwbf_batch_create([job], warps_per_cta=warps_per_cta, packed=1)
+    batch = fwbf.fwbf_batch_create([job], warps_per_cta=warps_per_cta, packed=2)
     s = torch.cuda.Stream()
     try:
         with torch.cuda.stream(s):

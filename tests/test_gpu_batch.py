@@ -47,7 +47,7 @@ def _single(fwbf, j):
     return bits.cpu().numpy(), iters.cpu().numpy()
 
 
-@pytest.mark.parametrize("warps,packed", [(16, 1), (8, 1), (4, 1), (16, 0), (7, 0)])
+@pytest.mark.parametrize("warps,packed", [(16, 2), (16, 1), (8, 1), (4, 1), (16, 0), (7, 0)])
 def test_batch_equals_single_code_decoding(fwbf, jobs, warps, packed):
     outs = [j["code"].outputs(j["qd"].shape[0]) for j in jobs]
     spec = [(j["code"].handle, j["qd"], 60, 1.5, b, it) for j, (b, it) in zip(jobs, outs)]

@@ -205,15 +205,19 @@ def test_batched_learned_job_equals_single_code(fwbf):
             b2, i2 = code.outputs(F)
             specs.append((code.handle, qd, 60, 1.5, b2, i2) + ((net.blob, 4) if learned else ()))
             singles.append((b1, i1, b2, i2))
-        batch = fwbf.fwbf_batch_create(specs, warps_per_cta=16, packed=1)
-        try:
-            fwbf.fwbf_decode_batch(batch)
-            torch.cuda.synchronize()
-            assert fwbf.fwbf_batch_status() == 0
-        finally:
-            fwbf.fwbf_batch_destroy(batch)
-        for b1, i1, b2, i2 in singles:
-            assert torch.equal(i1, i2) and torch.equal(b1, b2)
+        for packed in (1, 2):  # one warp per frame where 16 fit a block; warp groups everywhere
+            for _, _, b2, i2 in singles:
+                b2.fill_(-1)
+                i2.fill_(-99)
+            batch = fwbf.fwbf_batch_create(specs, warps_per_cta=16, packed=packed)
+            try:
+                fwbf.fwbf_decode_batch(batch)
+                torch.cuda.synchronize()
+                assert fwbf.fwbf_batch_status() == 0
+            finally:
+                fwbf.fwbf_batch_destroy(batch)
+            for b1, i1, b2, i2 in singles:
+                assert torch.equal(i1, i2) and torch.equal(b1, b2), packed
     finally:
         for code in codes:
             code.close()
