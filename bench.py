@@ -416,7 +416,7 @@ def e2e(args, fwbf, code, y, w, F, enc, dev, stream):
 
     def step():
         fwbf.fwbf_decode_host(code.handle, y_host, w["max_iter"], w["alpha"], bits_host, iters_host,
-                              chunk_frames=1 << 17, stream=stream)
+                              chunk_frames=1 << 15, stream=stream)
 
     for _ in range(2):
         step()

@@ -194,7 +194,7 @@ def _host(t, dtype, name):
 
 
 def fwbf_decode_host(code, y_host, max_iter: int, alpha: float, bits_host, iters_host,
-                     chunk_frames: int = 1 << 17, stream=None) -> None:
+                     chunk_frames: int = 1 << 15, stream=None) -> None:
     """Host float frames -> host decisions, pipelined in chunks over two
     streams (pinned host tensors give overlapped copies)."""
     import torch
