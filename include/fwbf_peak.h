@@ -1,5 +1,7 @@
 /*
- * Integer issue-rate microbenchmark of the GPU the decoder runs on.
+ * Diagnostics of the GPU the decoder runs on (not part of the decoding method).
+ *
+ * Integer issue-rate microbenchmark.
  *
  * Not part of the decoding method (the paper has no counterpart): it measures
  * the denominator of the decoder's roofline.  FWBF decoding (Sec. III) is
@@ -33,6 +35,23 @@ extern "C" {
  * FWBF_ECUDA for a CUDA error.
  */
 int fwbf_peak_int_issue(int mix, double ms, void *stream, double *out_ops_per_s, double *out_ops);
+
+/*
+ * Bounded-wait probe (for tests of the timeout path without a GPU fault): one
+ * block of 32 threads runs the bounded mbarrier wait that every decoding
+ * kernel uses while its code tables are staged into shared memory, on a
+ * barrier that expects expect_bytes bytes.  No copy is issued, so with
+ * expect_bytes > 0 nothing completes the barrier: the wait gives up after its
+ * limit (one second of the GPU's global timer) and the kernel records
+ * FWBF_ETIMEOUT -- what a decoding kernel reports through fwbf_last_status /
+ * fwbf_batch_status when a table copy does not land -- and returns, leaving
+ * the context usable.  With expect_bytes = 0 the barrier completes at once
+ * (FWBF_OK).  Not part of the method.
+ *   expect_bytes  0..65536
+ *   out_status    host int: FWBF_OK or FWBF_ETIMEOUT
+ * Blocks until the kernel has finished.  Returns 0, FWBF_EINVAL or FWBF_ECUDA.
+ */
+int fwbf_probe_bounded_wait(uint32_t expect_bytes, void *stream, int *out_status);
 
 #ifdef __cplusplus
 }

@@ -6,6 +6,7 @@
 // issue throughput.
 #include <cuda_runtime.h>
 
+#include "device_common.cuh"
 #include "fwbf.h"
 #include "fwbf_internal.h"
 #include "fwbf_peak.h"
@@ -43,10 +44,45 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm)
     if (acc == 0x2545f491u) sink[0] = acc;  // keeps every chain live
 }
 
+// The table-staging wait of the decoders on a barrier expecting bytes that no
+// copy delivers (expect_bytes > 0): the bounded wait gives up and the status
+// records the timeout.
+__global__ void bounded_wait_probe_kernel(int *status, uint32_t expect_bytes) {
+    __shared__ uint64_t bar;
+    __shared__ int flag;
+    if (threadIdx.x == 0) {
+        flag = 0;
+        mbar_init(&bar, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, expect_bytes);
+    if (!mbar_wait_bounded(&bar, 0, kWaitLimitNs)) atomicOr(&flag, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) *status = flag ? FWBF_ETIMEOUT : FWBF_OK;
+}
+
 }  // namespace
 }  // namespace fwbf
 
 using namespace fwbf;
+
+extern "C" int fwbf_probe_bounded_wait(uint32_t expect_bytes, void *stream, int *out_status) {
+    if (expect_bytes > 65536u || !out_status)
+        return fail(FWBF_EINVAL, "fwbf_probe_bounded_wait: expect_bytes <= 65536 and a result pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *d_status = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_status), sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(status)");
+    bounded_wait_probe_kernel<<<1, 32, 0, s>>>(d_status, expect_bytes);
+    e = cudaGetLastError();
+    int h = -1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d_status, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait probe");
+    *out_status = h;
+    return FWBF_OK;
+}
 
 extern "C" int fwbf_peak_int_issue(int mix, double ms, void *stream, double *out_ops_per_s, double *out_ops) {
     if ((mix != 0 && mix != 1) || !(ms >= 1.0 && ms <= 10000.0) || !out_ops_per_s)

@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_decode_lambda": ([P, P, i64, i32, f32, i32, P, P, P], ctypes.c_int),
         "fwbf_decode_host": ([P, P, i64, i32, f32, P, P, i64, P], ctypes.c_int),
         "fwbf_peak_int_issue": ([ctypes.c_int, ctypes.c_double, P, P, P], ctypes.c_int),
+        "fwbf_probe_bounded_wait": ([ctypes.c_uint32, P, P], ctypes.c_int),
         "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
         "fwbf_decode_sched": ([P, P, i64, i32, P, P, i64, P, P, P, i32, P], ctypes.c_int),
         "fwbf_decode_learned": ([P, P, i64, i32, i32, f32, P, P, P, P, P, i32, P], ctypes.c_int),
@@ -213,6 +214,14 @@ def fwbf_peak_int_issue(mix: int, ms: float = 200.0, stream=None) -> float:
     r = ctypes.c_double(0.0)
     _check(load_library().fwbf_peak_int_issue(int(mix), float(ms), _stream(stream), ctypes.byref(r), None))
     return r.value
+
+
+def fwbf_probe_bounded_wait(expect_bytes: int, stream=None) -> int:
+    """Runs the decoders' bounded table-staging wait on a barrier expecting
+    expect_bytes that no copy delivers; returns FWBF_OK or FWBF_ETIMEOUT."""
+    st = ctypes.c_int(-1)
+    _check(load_library().fwbf_probe_bounded_wait(int(expect_bytes), _stream(stream), ctypes.byref(st)))
+    return st.value
 
 
 def fwbf_decode_lambda(code, y, max_iter: int, alpha: float, lam: int, out_bits, out_iters, stream=None) -> None:

@@ -121,3 +121,11 @@ def test_peak_probe_rejects_bad_arguments(lib):
     assert lib.fwbf_peak_int_issue(2, 100.0, None, ctypes.byref(r), None) == fwbf.FWBF_EINVAL
     assert lib.fwbf_peak_int_issue(1, 0.5, None, ctypes.byref(r), None) == fwbf.FWBF_EINVAL
     assert lib.fwbf_peak_int_issue(1, 100.0, None, None, None) == fwbf.FWBF_EINVAL
+
+
+def test_bounded_wait_probe_rejects_bad_arguments(lib):
+    from paper_1206_3362_gb300 import fwbf
+
+    st = ctypes.c_int(0)
+    assert lib.fwbf_probe_bounded_wait(65537, None, ctypes.byref(st)) == fwbf.FWBF_EINVAL
+    assert lib.fwbf_probe_bounded_wait(16, None, None) == fwbf.FWBF_EINVAL
