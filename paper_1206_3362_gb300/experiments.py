@@ -10,6 +10,8 @@
   Eb/N0 for two block lengths and K_max = 5 and 10 (the paper notes that 5 and 10
   iterations are not distinctly apart).
 
+* ``sweep1``: plain FWBF on EG(1023,781) over 3.0-5.0 dB in 0.25 dB steps
+  (FER, BER, passes, throughput per point).
 * ``scale4``: learned + batched at scale: the rate-0.94 quasi-cyclic N = 16384
   code (column weight 4, circulants of 512) and EG(4095,3367), 2^22 frames over
   4.0-5.5 dB, one graph-captured batched launch with autotuned block lengths
@@ -21,6 +23,7 @@
     python -m paper_1206_3362_gb300.experiments tab1 [--frames N]
     python -m paper_1206_3362_gb300.experiments eg255 [--frames N]
     python -m paper_1206_3362_gb300.experiments scale4 [--frames N]
+    python -m paper_1206_3362_gb300.experiments sweep1 [--frames N]
 """
 from __future__ import annotations
 
@@ -81,6 +84,45 @@ def eg255(frames: int = 1 << 17, alpha: float = 1.5, ebn0=(3.0, 3.5, 4.0, 4.5, 5
         out["rows"][f"{eb}dB"] = {f"p{p}_kmax{k}": _run(codes[p], q, c, k, alpha) for p in (16, 51) for k in (5, 10)}
     for code in codes.values():
         code.close()
+    return out
+
+
+def sweep1(frames: int = 1 << 20, p: int = 31, alpha: float = 1.5, max_iter: int = 100,
+           ebn0=tuple(3.0 + 0.25 * i for i in range(9))):
+    """Plain FWBF on EG(1023,781) over 3.0-5.0 dB: FER (Wilson 95 % interval),
+    BER over the information bits and over all N bits, converged passes,
+    decode time and decoded information Gb/s per point."""
+    import torch
+
+    from .inputs import Encoder, make_code
+
+    h = make_code("eg1023")
+    enc = Encoder(h)
+    info = torch.as_tensor(enc.info_pos, device="cuda")
+    out = {"code": "eg1023", "p": p, "alpha": alpha, "max_iter": max_iter, "frames": frames, "rows": {}}
+    with fwbf.Code.from_parity_check(h, p) as code:
+        for i, eb in enumerate(ebn0):
+            q, c = make_frames(code, enc, frames, (eb,), seed=1100 + i, device="cuda")
+            bits, iters = code.outputs(frames, q.device)
+            fwbf.fwbf_decode(code.handle, q, max_iter, alpha, bits, iters)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fwbf.fwbf_decode(code.handle, q, max_iter, alpha, bits, iters)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            ok = frame_ok(bits, iters, c)
+            fe = int((~ok).sum().item())
+            wrong = unpack_bits_torch(bits, h.N) != c
+            conv = iters >= 0
+            out["rows"][f"{eb}dB"] = {
+                "fer": fe / frames, "fer_ci95": wilson(fe, frames),
+                "ber_info": float(wrong[:, info].float().mean().item()),
+                "ber_all": float(wrong.float().mean().item()),
+                "avg_passes_converged": float(iters[conv].float().mean().item()) if conv.any() else None,
+                "decode_ms": ms, "gbps": frames * enc.K / ms / 1e6}
+            del q, c, bits, iters, wrong
     return out
 
 
@@ -242,7 +284,7 @@ def main():
     import __graft_entry__
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["tab1", "eg255", "scale4"])
+    ap.add_argument("what", choices=["tab1", "eg255", "scale4", "sweep1"])
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
@@ -252,6 +294,8 @@ def main():
         res = tab1(args.frames or (1 << 16))
     elif args.what == "eg255":
         res = eg255(args.frames or (1 << 17))
+    elif args.what == "sweep1":
+        res = sweep1(args.frames or (1 << 20))
     else:
         res = scale4(args.frames or (1 << 22))
     text = json.dumps(res, indent=1)

@@ -61,3 +61,29 @@ def test_scale4_small(built):
         assert rows[("eg4095", 5.5)][arm]["fer"] <= 0.01
         for r in out["jobs"]:
             assert 0.0 <= r[arm]["ber"] <= r[arm]["fer"] <= 1.0
+
+
+def test_sweep1_small(built):
+    """The EG(1023,781) sweep: FER falls monotonically over 3.0-5.0 dB (a
+    statistical band: at 4096 frames the points are far apart), and a few
+    frames of each point match the oracle exactly."""
+    import numpy as np
+
+    import oracle
+    from paper_1206_3362_gb300 import experiments, fwbf
+    from paper_1206_3362_gb300.inputs import Encoder, make_code
+    from paper_1206_3362_gb300.learned import make_frames
+
+    out = experiments.sweep1(frames=4096, ebn0=(3.0, 4.0, 5.0))
+    fer = [out["rows"][f"{eb}dB"]["fer"] for eb in (3.0, 4.0, 5.0)]
+    assert fer[0] > fer[1] >= fer[2]
+    for r in out["rows"].values():
+        assert r["ber_all"] <= r["fer"] and r["gbps"] > 0
+    h = make_code("eg1023")
+    enc = Encoder(h)
+    with fwbf.Code.from_parity_check(h, 31) as code:
+        q, c = make_frames(code, enc, 64, (3.5,), seed=77, device="cuda")
+        bits, iters = code.decode(q, 100, 1.5)
+        torch.cuda.synchronize()
+    bo, io = oracle.fwbf_i8(h, 31, q.cpu().numpy(), 100, 1.5)
+    assert np.array_equal(iters.cpu().numpy(), io) and np.array_equal(bits.cpu().numpy().view(np.uint32), bo)
