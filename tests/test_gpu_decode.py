@@ -327,3 +327,56 @@ def test_decode_host_pipeline(fwbf):
             torch.cuda.synchronize()
             assert np.array_equal(ih.numpy(), io), chunk
             assert np.array_equal(bh.numpy().view(np.uint32), bo), chunk
+
+
+def test_zero_frames_every_entry_point(fwbf):
+    """n_frames = 0 is a no-op for every decoding entry point and for a batch
+    job, and leaves the status clean."""
+    from paper_1206_3362_gb300.learned import Network
+
+    h = make_code("eg255")
+    net = Network(seed=1)
+    with fwbf.Code.from_parity_check(h, 16) as code:
+        q0 = torch.empty((0, h.N), dtype=torch.int8, device="cuda")
+        y0 = torch.empty((0, h.N), dtype=torch.float32, device="cuda")
+        bits, iters = code.outputs(0)
+        fwbf.fwbf_decode(code.handle, q0, 10, 1.5, bits, iters)
+        fwbf.fwbf_decode_noalloc(code.handle, q0, 10, 1.5, bits, iters)
+        fwbf.fwbf_decode_f32(code.handle, y0, 10, 1.5, bits, iters)
+        fwbf.fwbf_decode_lambda(code.handle, q0, 10, 1.5, 4, bits, iters)
+        a0 = torch.empty((0, 10), dtype=torch.int32, device="cuda")
+        fwbf.fwbf_decode_sched(code.handle, q0, 10, a0, a0, bits, iters)
+        fwbf.fwbf_decode_learned(code.handle, q0, 10, 4, 1.5, net.blob, bits, iters)
+        fwbf.fwbf_decode_host(code.handle, torch.empty((0, h.N), dtype=torch.float32), 10, 1.5,
+                              torch.empty((0, code.words), dtype=torch.int32), torch.empty(0, dtype=torch.int32))
+        h2, c2, y2 = frames("eg255", 3, 4.0, seed=2)
+        q2 = torch.from_numpy(oracle.quantize(y2)).cuda()
+        b2, i2 = code.outputs(3)
+        batch = fwbf.fwbf_batch_create([(code.handle, q0, 10, 1.5, bits, iters), (code.handle, q2, 10, 1.5, b2, i2)])
+        try:
+            fwbf.fwbf_decode_batch(batch)
+            torch.cuda.synchronize()
+            assert fwbf.fwbf_batch_status() == 0
+        finally:
+            fwbf.fwbf_batch_destroy(batch)
+        bo, io = oracle.fwbf_i8(h, 16, oracle.quantize(y2), 10, 1.5)
+        assert np.array_equal(i2.cpu().numpy(), io)
+        torch.cuda.synchronize()
+        assert fwbf.fwbf_last_status() == 0
+
+
+def test_code_beyond_shared_memory_is_rejected(fwbf):
+    """A code whose frame state does not fit one block's shared memory (random
+    (3,6) N = 40,000: ~290 KB per frame) is rejected with FWBF_EUNSUPPORTED
+    before anything is launched; the next call decodes normally."""
+    from paper_1206_3362_gb300.inputs.codes import random_regular
+
+    h = random_regular(40000, 3, 6, seed=64)
+    with fwbf.Code.from_parity_check(h, 32) as code:
+        q = torch.zeros((2, h.N), dtype=torch.int8, device="cuda")
+        bits, iters = code.outputs(2)
+        with pytest.raises(fwbf.FwbfError) as err:
+            fwbf.fwbf_decode(code.handle, q, 10, 1.5, bits, iters)
+        assert err.value.status == fwbf.FWBF_EUNSUPPORTED
+    h, c, y = frames("eg255", 20, 4.0, seed=65)
+    assert_same(fwbf, h, 16, oracle.quantize(y), 10, 1.5)
