@@ -38,7 +38,7 @@ WORKLOAD = dict(code="eg1023", ebn0_db=4.0, frames=1 << 20, max_iter=100, seg_le
 # of DECODE_KERNEL (131,072 frames of this workload; scaled by frames, since
 # traffic is the frame bytes in and the decisions out); see
 # profiles/fwbf_decode_i8_eg1023_4dB.md.  Set to None when the kernel changes.
-DECODE_TRAFFIC_BYTES_PER_FRAME = (134.236160e6 + 8.584448e6) / 131072
+DECODE_TRAFFIC_BYTES_PER_FRAME = (134.140928e6 + 8.588800e6) / 131072
 DECODE_KERNEL = "fwbf_decode_i8_cyclic_kernel<4, 2, true>"
 
 

@@ -55,6 +55,10 @@ typedef struct {
     int32_t seg_len;    /* p, block length of the bit-choose */
     int32_t n_blocks;   /* ceil(N / p) */
     int64_t table_bytes;/* device bytes of the index tables */
+    int32_t max_row_overlap; /* most bits any two checks share: the RC constraint
+                                of Sec. II (no two rows with two common ones)
+                                holds iff this is <= 1; the decoder works either way */
+    int32_t reserved;
 } fwbf_code_info;
 
 /*

@@ -115,6 +115,35 @@ int fwbf_code_create(int32_t N, int32_t M, int64_t nnz, const int32_t *row_idx, 
     for (int n = 0; n < N; ++n) dv_max = std::max(dv_max, cw[n]);
     if (dc_max > 255 || dv_max > 255) return fail(FWBF_EUNSUPPORTED, "row or column weight above 255");
 
+    // RC constraint (Sec. II): the most bits two checks share, by counting for
+    // each check m the later checks met through each of its bits
+    int max_overlap = 0;
+    {
+        std::vector<int32_t> cptr(N + 1, 0), crow((size_t)nnz), rptr(M + 1, 0), rcol((size_t)nnz);
+        for (int n = 0; n < N; ++n) cptr[n + 1] = cptr[n] + cw[n];
+        for (int m = 0; m < M; ++m) rptr[m + 1] = rptr[m] + rw[m];
+        std::vector<int32_t> cf(cptr.begin(), cptr.end() - 1), rf(rptr.begin(), rptr.end() - 1);
+        for (uint32_t k : keys) {  // sorted by (row, column)
+            const int m = (int)(k >> 16), n = (int)(k & 0xffffu);
+            crow[cf[n]++] = m;
+            rcol[rf[m]++] = n;
+        }
+        std::vector<int32_t> cnt(M, 0), touched;
+        for (int m = 0; m < M; ++m) {
+            touched.clear();
+            for (int32_t e = rptr[m]; e < rptr[m + 1]; ++e) {
+                const int n = rcol[e];
+                for (int32_t f = cptr[n]; f < cptr[n + 1]; ++f) {
+                    const int r = crow[f];
+                    if (r <= m) continue;
+                    if (cnt[r]++ == 0) touched.push_back(r);
+                    max_overlap = std::max(max_overlap, cnt[r]);
+                }
+            }
+            for (int r : touched) cnt[r] = 0;
+        }
+    }
+
     const int Z = detect_circulant(N, M, nnz, row_idx, col_idx);
     const int MB = M / Z, NB = N / Z;
     // circulant entries per block row / block column
@@ -162,6 +191,7 @@ int fwbf_code_create(int32_t N, int32_t M, int64_t nnz, const int32_t *row_idx, 
     c->NB = NB;
     c->dv_max = dv_max;
     c->dc_max = dc_max;
+    c->max_row_overlap = max_overlap;
     c->p = seg_len;
     c->B = (N + seg_len - 1) / seg_len;
     c->p_magic = magic_for((uint32_t)seg_len);
@@ -212,6 +242,8 @@ int fwbf_code_query(fwbf_code c, fwbf_code_info *out) {
     out->seg_len = c->p;
     out->n_blocks = c->B;
     out->table_bytes = (int64_t)c->table_words * 4;
+    out->max_row_overlap = c->max_row_overlap;
+    out->reserved = 0;
     return FWBF_OK;
 }
 

@@ -21,6 +21,7 @@ struct fwbf_code_s {
     int64_t nnz;
     int Z, MB, NB;
     int dv_max, dc_max;
+    int max_row_overlap;        // most bits two checks share (RC constraint iff <= 1)
     int p, B;
     uint32_t p_magic, z_magic;  // ceil(2^32 / d) for exact x / d with x < 65536
     uint32_t rptr_off, rent_off, cptr_off, cent_off;

@@ -40,7 +40,7 @@ class CodeInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("Z", ctypes.c_int32), ("dv_max", ctypes.c_int32), ("dc_max", ctypes.c_int32),
                 ("seg_len", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
-                ("table_bytes", ctypes.c_int64)]
+                ("table_bytes", ctypes.c_int64), ("max_row_overlap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -384,8 +384,20 @@ class Code:
         self.words = (N + 31) // 32
 
     @classmethod
-    def from_parity_check(cls, h, seg_len: int) -> "Code":
-        return cls(h.N, h.M, h.rows, h.cols, seg_len)
+    def from_parity_check(cls, h, seg_len: int, require_rc: bool = False) -> "Code":
+        """Handle for ParityCheck h.  A code that breaks the RC constraint (two
+        checks sharing two or more bits, i.e. 4-cycles) gets a warning, or with
+        require_rc=True a ValueError."""
+        code = cls(h.N, h.M, h.rows, h.cols, seg_len)
+        overlap = code.info.max_row_overlap
+        if overlap > 1:
+            if require_rc:
+                code.close()
+                raise ValueError(f"H breaks the RC constraint: two checks share {overlap} bits")
+            import warnings
+
+            warnings.warn(f"H breaks the RC constraint: two checks share {overlap} bits", stacklevel=2)
+        return code
 
     def close(self):
         if self.handle:

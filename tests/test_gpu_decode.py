@@ -380,3 +380,35 @@ def test_code_beyond_shared_memory_is_rejected(fwbf):
         assert err.value.status == fwbf.FWBF_EUNSUPPORTED
     h, c, y = frames("eg255", 20, 4.0, seed=65)
     assert_same(fwbf, h, 16, oracle.quantize(y), 10, 1.5)
+
+
+def test_rc_constraint_reported(fwbf):
+    """fwbf_code_info.max_row_overlap: 1 for the EG and QC codes (any two lines
+    of a Euclidean geometry meet in at most one point), at most 1 for the
+    4-cycle-free random code, 2 for an H with a 4-cycle (warned, or rejected on
+    request); the decoder still matches the oracle on that H."""
+    import warnings
+
+    from paper_1206_3362_gb300.inputs.codes import ParityCheck
+
+    for key in ("eg255", "eg1023", "qc8192"):
+        with fwbf.Code.from_parity_check(make_code(key), 16) as code:
+            assert code.info.max_row_overlap == 1, key
+    with fwbf.Code.from_parity_check(make_code("rand504"), 32) as code:
+        assert code.info.max_row_overlap <= 1
+    # checks 0 and 1 share bits 0 and 1
+    rows = np.array([0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3], dtype=np.int32)
+    cols = np.array([0, 1, 2, 0, 1, 3, 2, 4, 5, 3, 4, 5], dtype=np.int32)
+    h = ParityCheck(N=6, M=4, rows=rows, cols=cols)
+    with warnings.catch_warnings(record=True) as w:
+        warnings.simplefilter("always")
+        code = fwbf.Code.from_parity_check(h, 2)
+    assert code.info.max_row_overlap == 2 and any("RC constraint" in str(x.message) for x in w)
+    q = np.array([[10, -3, 7, 20, -5, 9], [-12, -12, 4, 4, 4, -4]], dtype=np.int8)
+    bits, iters = code.decode(torch.from_numpy(q).cuda(), 8, 1.0)
+    torch.cuda.synchronize()
+    code.close()
+    bo, io = oracle.fwbf_i8(h, 2, q, 8, 1.0)
+    assert np.array_equal(iters.cpu().numpy(), io) and np.array_equal(bits.cpu().numpy().view(np.uint32), bo)
+    with pytest.raises(ValueError):
+        fwbf.Code.from_parity_check(h, 2, require_rc=True)
