@@ -83,8 +83,6 @@ int read_and_clear_status_i8(cudaStream_t s, int *out) {
     return 0;
 }
 
-static inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
-
 // Generic (any H) int8 decoder launch with a caller-provided frame counter
 // that is already zero on the stream.
 static int launch_generic_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,

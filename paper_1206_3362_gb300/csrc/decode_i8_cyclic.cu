@@ -71,8 +71,6 @@ __global__ void __launch_bounds__(512, WPF == 2 ? 2 : 1) fwbf_decode_i8_cyclic_k
     }
 }
 
-static inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
-
 bool cyclic_eligible(const fwbf_code_s *c) {
     if (c->Z != c->N || c->N != c->M || c->MB != 1 || c->NB != 1) return false;
     const int H = (c->Z + 1) / 2;
