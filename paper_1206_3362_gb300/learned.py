@@ -261,9 +261,10 @@ def make_frames(code_h, enc, F, ebn0_list, seed, device):
 
 
 def train_pipeline(code, enc, train_frames: int, ebn0_list, sch: Schedule, epochs: int = 4, seed: int = 1,
-                   lr: float = 2e-3, log=print):
+                   lr: float = 2e-3, log=print, oversample: int = 1):
     """Labels -> features -> training, all on the GPU.  Returns the network and
-    a summary."""
+    a summary.  oversample > 1 repeats every sample whose label differs from
+    the default that many times (the labels are mostly the default)."""
     import torch
 
     t0 = time.time()
@@ -272,6 +273,10 @@ def train_pipeline(code, enc, train_frames: int, ebn0_list, sch: Schedule, epoch
     torch.cuda.synchronize()
     t_label = time.time() - t0
     X, Y = training_set(code, q, A, T, sch)
+    if oversample > 1:
+        rare = (Y[:, 0] != alpha_q(sch.alpha_default) / 256.0) | (Y[:, 1] != 0.0)
+        X = torch.cat([X] + [X[rare]] * (oversample - 1)).contiguous()
+        Y = torch.cat([Y] + [Y[rare]] * (oversample - 1)).contiguous()
     changed = float(((A[:, :sch.k_learn] != alpha_q(sch.alpha_default)) | (T[:, :sch.k_learn] != 0)).float().mean())
     net = Network(seed=seed, alpha_default=sch.alpha_default)
     g = torch.Generator(device="cuda")
@@ -351,6 +356,7 @@ def main():
     ap.add_argument("--out", default=None, help="weights file (default: weights/fwbf_mlp_<code>.npz)")
     ap.add_argument("--report", default=None)
     ap.add_argument("--weights", default=None, help="evaluate these weights instead of training")
+    ap.add_argument("--oversample", type=int, default=1, help="repeat non-default labels this many times")
     args = ap.parse_args()
     torch.cuda.set_device(0)
     h = make_code(args.code)
@@ -372,7 +378,7 @@ def main():
             code = fwbf.Code.from_parity_check(h, p_star)
     else:
         net, summary = train_pipeline(code, enc, args.train_frames, ebn0, sch, epochs=args.epochs,
-                                      log=lambda m: print(m, flush=True))
+                                      log=lambda m: print(m, flush=True), oversample=args.oversample)
         net.save(out_path, seg_len=p_star, k_learn=sch.k_learn, alpha_default=sch.alpha_default)
     res = {"code": args.code, "autotune": tune, "train": summary, "seg_len": p_star, "alpha": a_star,
            "k_learn": sch.k_learn}
