@@ -2,13 +2,13 @@
 // its own frames and outputs (codes of different N, M and row / column
 // weight in the same launch).
 //
-// The batch handle holds a device table of jobs (one per code) and one frame
-// counter per job.  Every CTA walks the jobs, starting at job
-// blockIdx.x mod n_jobs so that CTAs spread over the codes: for each job with
-// frames left it copies the job descriptor into shared memory, stages that
-// code's index tables with a bulk copy (TMA) on a fresh mbarrier, lays its
-// warps' shared-memory slices out for that code and lets each warp pull frames
-// from the job's counter until the job is exhausted; then the CTA moves on.
+// The batch handle holds the table of jobs (one per code; passed whole as the
+// launch's parameter block) and one device frame counter per job.  Every CTA
+// walks the jobs, starting at job blockIdx.x mod n_jobs so that CTAs spread
+// over the codes: for each job with frames left it stages that code's index
+// tables with a bulk copy (TMA) on a fresh mbarrier, lays its warps' shared-
+// memory slices out for that code and lets each warp (or warp group) pull
+// frames from the job's counter until the job is exhausted; then the CTA moves on.
 // Per frame a warp runs the packed cyclic decoder (cyclic codes) or the
 // generic list decoder (every other code) -- the same device code as the
 // single-code kernels, so results are identical to fwbf_decode.
@@ -42,6 +42,14 @@ struct BatchJob {
 };
 
 constexpr int kMaxJobs = 16;
+
+// The whole job table travels as the launch's parameter block (constant
+// space, 16 x 424 bytes): the frame code reads its job's fields without
+// touching shared memory, which the decoders keep busy.
+struct BatchParams {
+    BatchJob jobs[kMaxJobs];
+    int n_jobs;
+};
 
 // The CTA's frames of a cyclic job decoded by groups of WPF warps, R pairs
 // per lane per chunk (group g meets at named barrier 1 + g; the CTA-wide
@@ -108,24 +116,21 @@ __device__ __forceinline__ void batch_generic_dispatch(const BatchJob &J, const 
 // GROUPED: every job runs warp groups (two blocks of 512 threads per SM, 64
 // registers); otherwise any mix of one-warp and group jobs (one block per SM).
 template <bool GROUPED>
-__global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel(const BatchJob *__restrict__ jobs,
-                                                                                  int n_jobs) {
+__global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bars[kMaxJobs];
     __shared__ int flag;
-    __shared__ BatchJob J;
     __shared__ __align__(16) uint32_t d_off[128], u_off[128];  // read as 8- and 16-byte vectors
     __shared__ int live;
     __shared__ unsigned long long fslot[16];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    const int n_jobs = bp.n_jobs;
     for (int t = 0; t < n_jobs; ++t) {
         const int j = (blockIdx.x + t) % n_jobs;
-        if (threadIdx.x == 0) {
-            J = jobs[j];
-            live = atomicAdd(J.counter, 0ull) < (unsigned long long)J.F;
-        }
+        const BatchJob &J = bp.jobs[j];
+        if (threadIdx.x == 0) live = atomicAdd(J.counter, 0ull) < (unsigned long long)J.F;
         __syncthreads();
         if (!live) {
             __syncthreads();
@@ -191,7 +196,7 @@ using namespace fwbf;
 struct fwbf_batch_s {
     int n_jobs = 0;
     bool grouped = false;
-    BatchJob *d_jobs = nullptr;
+    BatchParams params{};
     unsigned long long *d_counters = nullptr;
     int blocks = 0, threads = 0;
     uint32_t dyn = 0;
@@ -350,7 +355,6 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
     bh->threads = grouped ? 512 : 32 * warps_per_cta;
     bh->dyn = dyn;
     e = cudaMalloc(reinterpret_cast<void **>(&bh->d_counters), sizeof(unsigned long long) * n_jobs);
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&bh->d_jobs), sizeof(BatchJob) * n_jobs);
     if (e != cudaSuccess) {
         cudaFree(bh->d_counters);
         delete bh;
@@ -360,15 +364,15 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         hj[j].counter = bh->d_counters + j;
         hj[j].gp.counter = hj[j].counter;
         hj[j].cp.counter = hj[j].counter;
+        bh->params.jobs[j] = hj[j];
     }
-    e = cudaMemcpy(bh->d_jobs, hj.data(), sizeof(BatchJob) * n_jobs, cudaMemcpyHostToDevice);
-    void (*kern)(const BatchJob *, int) = grouped ? fwbf_decode_batch_kernel<true> : fwbf_decode_batch_kernel<false>;
+    bh->params.n_jobs = n_jobs;
+    void (*kern)(const BatchParams) = grouped ? fwbf_decode_batch_kernel<true> : fwbf_decode_batch_kernel<false>;
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bh->threads, dyn);
     if (e != cudaSuccess || per_sm < 1) {
         cudaFree(bh->d_counters);
-        cudaFree(bh->d_jobs);
         delete bh;
         return e != cudaSuccess ? cuda_fail(e, "batch set-up") : fail(FWBF_EUNSUPPORTED, "batch kernel does not fit");
     }
@@ -383,9 +387,9 @@ int fwbf_decode_batch(fwbf_batch b, void *stream) {
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * b->n_jobs, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counters)");
     if (b->grouped)
-        fwbf_decode_batch_kernel<true><<<b->blocks, b->threads, b->dyn, s>>>(b->d_jobs, b->n_jobs);
+        fwbf_decode_batch_kernel<true><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
     else
-        fwbf_decode_batch_kernel<false><<<b->blocks, b->threads, b->dyn, s>>>(b->d_jobs, b->n_jobs);
+        fwbf_decode_batch_kernel<false><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
     e = cudaGetLastError();
     return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "decode_batch launch");
 }
@@ -394,7 +398,6 @@ int fwbf_batch_destroy(fwbf_batch b) {
     if (!b) return FWBF_OK;
     cudaError_t e = cudaDeviceSynchronize();
     cudaFree(b->d_counters);
-    cudaFree(b->d_jobs);
     delete b;
     return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "cudaDeviceSynchronize");
 }
