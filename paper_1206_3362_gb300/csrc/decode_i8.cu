@@ -144,6 +144,8 @@ static int launch_i8_with_counter(const fwbf_code_s *c, const int8_t *y, int64_t
                                   unsigned long long *counter, cudaStream_t s) {
     if (cyclic_eligible(c))
         return launch_decode_i8_cyclic(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
+    if (qc_eligible(c))
+        return launch_decode_i8_qc(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
     return launch_generic_i8(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
 }
 

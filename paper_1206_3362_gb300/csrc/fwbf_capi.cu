@@ -429,14 +429,16 @@ int fwbf_metric_f32(fwbf_code c, const float *y, int64_t n_frames, float alpha, 
 }
 
 int fwbf_last_status(void *stream) {
-    int a = 0, b = 0, c = 0;
+    int a = 0, b = 0, c = 0, d = 0;
     int rc = read_and_clear_status_i8(static_cast<cudaStream_t>(stream), &a);
     if (rc) return rc;
     rc = read_and_clear_status_f32(static_cast<cudaStream_t>(stream), &b);
     if (rc) return rc;
     rc = read_and_clear_status_i8_cyclic(static_cast<cudaStream_t>(stream), &c);
     if (rc) return rc;
-    return (a || b || c) ? fail(FWBF_ETIMEOUT, "a kernel gave up waiting for its table copy") : FWBF_OK;
+    rc = read_and_clear_status_i8_qc(static_cast<cudaStream_t>(stream), &d);
+    if (rc) return rc;
+    return (a || b || c || d) ? fail(FWBF_ETIMEOUT, "a kernel gave up waiting for its table copy") : FWBF_OK;
 }
 
 }  // extern "C"

@@ -49,6 +49,11 @@ int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, in
                      cudaStream_t s);
 bool cyclic_eligible(const fwbf_code_s *c);
 int read_and_clear_status_i8_cyclic(cudaStream_t s, int *out);
+bool qc_eligible(const fwbf_code_s *c);
+int read_and_clear_status_i8_qc(cudaStream_t s, int *out);
+int launch_decode_i8_qc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                        int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
+                        cudaStream_t s);
 // per-pass parameters of the cyclic decoder (mode 0: fixed, 1: schedule arrays,
 // 2: learned network with plain fallback)
 struct CyclicModes {

@@ -1,0 +1,262 @@
+// Per-frame body of the packed int8 FWBF decoder for quasi-cyclic codes: H
+// made of MB x NB blocks of Z x Z circulants (each block a sum of circulant
+// permutations), Z a multiple of 64.  The same exact reformulation as the
+// cyclic decoder (paper Sec. III, Eq. 1 in fixed point), carried over to
+// several circulant blocks:
+//
+//   * bit n = (block column c, j), check m = (block row r, i); positions j and
+//     j + H (H = Z/2) of a block column, and checks i and i + H of a block
+//     row, share one 32-bit word (two 16-bit halves).
+//   * check pass (once per frame): for every check pair, over the row's
+//     entries (c, t) -- bits (c, (i + t) mod Z) -- the packed key
+//     |q| << 8 | sign << 7 | entry gives min1 / arg-min and min2 by packed
+//     min/max, the sign bits the parity; records crec[m] = min1 | diff << 8 |
+//     arg-min bit << 16, and the signed arg-min corrections per bit in SC.
+//   * per pass: V'_m = (2 s_m - 1) min1_m + 128 lives in a doubled pair array
+//     per block row (X2r[k] = V'(r, k mod Z) | V'(r, (k + H) mod Z) << 16), so
+//     a bit pair gathers over its column's entries (r, t') with one aligned,
+//     conflict-free load each: D_n = G_n - 128 d_v + SC_n - 0x4000, metric
+//     E' = 256 D_n - alpha_q |q_n|.
+//   * flips toggle the syndrome and keep V' and SC current with atomics; a
+//     pass without flips ends the frame (its state would repeat to K_max).
+#pragma once
+
+#include "cyclic_frame.cuh"
+
+namespace fwbf {
+
+struct QcParams {
+    const uint32_t *table;
+    uint32_t table_words, table_smem_bytes;
+    uint32_t rptr_off, rent_off, cptr_off, cent_off;
+    int Z, H, MB, NB, XJ;  // XJ = Z + H - 1 words of the doubled array per block row
+    int dv;                // largest column weight
+    int p, B;
+    uint32_t p_magic, z_magic, h_magic;
+    const int8_t *y;
+    int64_t F;
+    int max_iter, alpha_q, theta_q;
+    uint32_t *out_bits;
+    int32_t *out_iters;
+    unsigned long long *counter;
+    uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys, off_red;
+};
+
+// arg-min correction slot of bit (c, a): pair word c * H + (a mod H), half a >= H
+__device__ __forceinline__ void qc_pair_slot(uint32_t c, uint32_t a, uint32_t H, uint32_t &idx, uint32_t &shift) {
+    const bool hi = a >= H;
+    idx = c * H + (hi ? a - H : a);
+    shift = hi ? 16u : 0u;
+}
+
+// Decodes frame f of P with a group of WPF warps (thread t of 32 * WPF); tbl
+// is the code's table blob staged in shared memory, ws the group's slice,
+// bar_id its named barrier (WPF > 1).
+template <int WPF>
+__device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl, unsigned char *ws, int t, int bar_id,
+                                         unsigned long long f) {
+    constexpr int G = 32 * WPF;
+    const int lane = t & 31, gw = t >> 5;
+    const uint32_t *rptr = tbl + P.rptr_off;
+    const uint32_t *rent = tbl + P.rent_off;
+    const uint32_t *cptr = tbl + P.cptr_off;
+    const uint32_t *cent = tbl + P.cent_off;
+    int8_t *stage = reinterpret_cast<int8_t *>(ws);
+    uint32_t *X2 = reinterpret_cast<uint32_t *>(ws + P.off_X);
+    uint32_t *crec = reinterpret_cast<uint32_t *>(ws + P.off_crec);
+    uint32_t *SC = reinterpret_cast<uint32_t *>(ws + P.off_SC);  // per bit pair, halves biased by 0x4000
+    uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
+    uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
+    int *red = reinterpret_cast<int *>(ws + P.off_red);
+    int rhalf = 0;
+    const uint32_t Z = (uint32_t)P.Z, H = (uint32_t)P.H;
+    const int MB = P.MB, NB = P.NB, XJ = P.XJ;
+    const int N = NB * (int)Z, M = MB * (int)Z;
+    const int Nw = N >> 5;
+    const int bias = 128 * P.dv + 0x4000;
+    const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
+    const uintptr_t ybase = reinterpret_cast<uintptr_t>(P.y);
+    const uintptr_t yend = ybase + (uintptr_t)(P.F * (int64_t)N);
+
+    // ---- frame load (aligned 16-byte chunks; byte loads at the buffer end)
+    const uintptr_t fb = ybase + (uintptr_t)(f * (unsigned long long)N);
+    const uintptr_t a0 = fb & ~(uintptr_t)15;
+    const int off = (int)(fb - a0);
+    const int nchunks = (off + N + 15) >> 4;
+    for (int c = t; c < nchunks; c += G) {
+        const uintptr_t src = a0 + (uintptr_t)c * 16;
+        uint4 v;
+        if (src + 16 <= yend) {
+            v = __ldcs(reinterpret_cast<const uint4 *>(src));
+        } else {
+            uint32_t wv[4] = {0u, 0u, 0u, 0u};
+            for (int i = 0; i < 16; ++i)
+                if (src + i < yend)
+                    wv[i >> 2] |= (uint32_t)(*reinterpret_cast<const unsigned char *>(src + i)) << (8 * (i & 3));
+            v = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+        *reinterpret_cast<uint4 *>(stage + c * 16) = v;
+    }
+    for (int i = t; i < NB * (int)H; i += G) SC[i] = 0x40004000u;
+    group_sync<WPF>(bar_id);
+    const int8_t *q = stage + off;
+    for (int w = gw; w < Nw; w += WPF) {
+        const int n = (w << 5) + lane;
+        const uint32_t zb = __ballot_sync(FULL, q[n] < 0);
+        if (lane == 0) zbits[w] = zb;
+    }
+
+    // ---- check pass: check pairs (r, i), (r, i + H); a warp's 32 lanes take
+    //      32 consecutive i of one block row (H is a multiple of 32) -----------
+    int W = 0;
+    for (int pi = t; pi < MB * (int)H; pi += G) {
+        const uint32_t r = div_small((uint32_t)pi, H, P.h_magic);
+        const uint32_t i = (uint32_t)pi - r * H;
+        const uint32_t e0 = rptr[r], e1 = rptr[r + 1];
+        uint32_t k1 = 0xffffffffu, k2 = 0xffffffffu, par = 0u;
+        uint32_t ek = 0u;  // the entry index in both halves
+        for (uint32_t e = e0; e < e1; ++e, ek += 0x10001u) {
+            const uint32_t ent = rent[e];
+            const uint32_t cZ = (ent >> 16) * Z;
+            uint32_t a = i + (ent & 0xffffu);
+            a = a >= Z ? a - Z : a;
+            uint32_t b = a + H;
+            b = b >= Z ? b - Z : b;
+            const int v1 = q[cZ + a], v2 = q[cZ + b];
+            const uint32_t key = qkey(v1) | (qkey(v2) << 16) | ek;
+            k2 = vmin_u16x2(k2, vmax_u16x2(k1, key));
+            k1 = vmin_u16x2(k1, key);
+            par ^= ((uint32_t)v1 & 0x80u) | (((uint32_t)v2 & 0x80u) << 16);
+        }
+        const uint32_t s_lo = (par >> 7) & 1u, s_hi = (par >> 23) & 1u;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const uint32_t ii = i + (half ? H : 0u);
+            const uint32_t a1 = k1 >> (16 * half), a2 = k2 >> (16 * half);
+            const uint32_t min1 = (a1 >> 8) & 0x7fu, pos = a1 & 0x7fu, min2 = (a2 >> 8) & 0x7fu;
+            const uint32_t diff = min2 - min1;
+            const uint32_t ent = rent[e0 + pos];
+            const uint32_t c = ent >> 16;
+            uint32_t a = ii + (ent & 0xffffu);
+            a = a >= Z ? a - Z : a;
+            crec[r * Z + ii] = min1 | (diff << 8) | ((c * Z + a) << 16);  // min1, diff, arg-min bit
+            if (diff) {
+                uint32_t idx, sh;
+                qc_pair_slot(c, a, H, idx, sh);
+                const int d = (half ? s_hi : s_lo) ? (int)diff : -(int)diff;
+                atomicAdd(&SC[idx], (uint32_t)d << sh);
+            }
+        }
+        const uint32_t slo = __ballot_sync(FULL, s_lo);
+        const uint32_t shi = __ballot_sync(FULL, s_hi);
+        if (lane == 0) {
+            sbits[(r * Z + i) >> 5] = slo;
+            sbits[(r * Z + i + H) >> 5] = shi;
+        }
+        W += __popc(slo) + __popc(shi);
+    }
+    W = group_sum3<WPF>(make_int3(W, 0, 0), red, rhalf, lane, gw, bar_id).x;  // (meets the group if WPF > 1)
+    if constexpr (WPF == 1) __syncwarp();
+
+    // the doubled arrays of V'_m = (2 s_m - 1) min1_m + 128, one per block row
+    for (int r = 0; r < MB; ++r) {
+        const uint32_t base = (uint32_t)r * Z;
+        build_doubled(X2 + r * XJ, (int)Z, (int)H, XJ, t, G, [&](int k) {
+            const uint32_t m = base + (uint32_t)k;
+            const uint32_t mn = crec[m] & 0x7fu;
+            return ((sbits[m >> 5] >> (m & 31)) & 1u) ? 128u + mn : 128u - mn;
+        });
+    }
+    group_sync<WPF>(bar_id);
+
+    // ---- iterations ------------------------------------------------------
+    int iters;
+    const int aq = P.alpha_q, tq = P.theta_q;
+    for (int k = 0;; ++k) {
+        if (W == 0) {
+            iters = k;
+            break;
+        }
+        if (k == P.max_iter) {
+            iters = -P.max_iter;
+            break;
+        }
+        // gather over the column's entries, then the per-block candidates
+        for (int pj = t; pj < NB * (int)H; pj += G) {
+            const uint32_t c = div_small((uint32_t)pj, H, P.h_magic);
+            const uint32_t j = (uint32_t)pj - c * H;
+            uint32_t acc = 0u;
+            for (uint32_t e = cptr[c]; e < cptr[c + 1]; ++e) {
+                const uint32_t ent = cent[e];
+                acc += X2[(ent >> 16) * (uint32_t)XJ + j + (ent & 0xffffu)];
+            }
+            const uint32_t SC2 = SC[pj];
+            // D_n >= 1 is necessary for E' > theta >= 0 (both halves at once)
+            const uint32_t cmask = (acc + SC2 + dfilter) & 0x80008000u;
+            if (cmask == 0u) continue;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const uint32_t n = c * Z + j + (half ? H : 0u);
+                const int Gv = (int)((acc >> (16 * half)) & 0xffffu);
+                const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
+                const int E = (Gv + sc - bias) * 256 - aq * abs((int)q[n]);
+                if (E > tq) {
+                    const uint32_t blk = div_small(n, P.p, P.p_magic);
+                    const unsigned long long key =
+                        ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - n);
+                    atomicMax(&keys[blk], key);
+                }
+            }
+        }
+        group_sync<WPF>(bar_id);
+        // flips: a thread per block; the flipped bit's checks one after another
+        int dW = 0, nflip = 0;
+        for (int b = t; b < P.B; b += G) {
+            const unsigned long long key = keys[b];
+            if (!key) continue;
+            keys[b] = 0ull;
+            ++nflip;
+            const uint32_t n = 0xffffffffu - (uint32_t)key;
+            atomicXor(&zbits[n >> 5], 1u << (n & 31));
+            const uint32_t c = div_small(n, Z, P.z_magic);
+            const uint32_t j = n - c * Z;
+            for (uint32_t e = cptr[c]; e < cptr[c + 1]; ++e) {
+                const uint32_t ent = cent[e];
+                const uint32_t r = ent >> 16;
+                uint32_t a = j + (ent & 0xffffu);
+                a = a >= Z ? a - Z : a;
+                const uint32_t m = r * Z + a;
+                const uint32_t bit = 1u << (m & 31);
+                const uint32_t old = atomicXor(&sbits[m >> 5], bit);
+                const bool now_set = !(old & bit);
+                dW += now_set ? 1 : -1;
+                const uint32_t rec = crec[m];
+                const int min1 = (int)(rec & 0x7fu), diff = (int)((rec >> 8) & 0x7fu);
+                doubled_add(X2 + r * XJ, (int)a, now_set ? 2 * min1 : -2 * min1, (int)Z, (int)H, XJ);
+                if (diff) {
+                    const uint32_t na = rec >> 16;
+                    const uint32_t ca = div_small(na, Z, P.z_magic);
+                    uint32_t idx, sh;
+                    qc_pair_slot(ca, na - ca * Z, H, idx, sh);
+                    const int d = now_set ? 2 * diff : -2 * diff;
+                    atomicAdd(&SC[idx], (uint32_t)d << sh);
+                }
+            }
+        }
+        const int3 tot = group_sum3<WPF>(make_int3(warp_sum(dW), warp_sum(nflip), 0), red, rhalf, lane, gw, bar_id);
+        W += tot.x;
+        if constexpr (WPF == 1) __syncwarp();
+        if (tot.y == 0) {  // fixed point: every later pass repeats this one
+            iters = -P.max_iter;
+            break;
+        }
+    }
+
+    uint32_t *ob = P.out_bits + f * (unsigned long long)Nw;
+    for (int w = t; w < Nw; w += G) __stcs(ob + w, zbits[w]);
+    if (t == 0) P.out_iters[f] = iters;
+    group_sync<WPF>(bar_id);
+}
+
+}  // namespace fwbf
