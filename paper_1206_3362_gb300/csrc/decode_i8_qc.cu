@@ -11,7 +11,7 @@ namespace fwbf {
 
 __device__ int g_status_i8_qc;
 
-template <int WPF>  // warps per frame
+template <int R, int WPF>  // pairs per lane per gather chunk, warps per frame
 __global__ void __launch_bounds__(768, 1) fwbf_decode_i8_qc_kernel(const __grid_constant__ QcParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(768, 1) fwbf_decode_i8_qc_kernel(const __grid_
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];  // rewritten only after the frame's last meeting
         if (f >= (unsigned long long)P.F) break;
-        qc_frame<WPF>(P, st, ws, t, bar_id, f);
+        qc_frame<R, WPF>(P, st, ws, t, bar_id, f);
     }
 }
 
@@ -129,10 +129,19 @@ int launch_decode_i8_qc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames,
     // up to 24 warps per block: 2, 4 or 8 warps per frame when fewer frames fit
     int wpf = 1;
     while (wpf < 8 && frames * wpf * 2 <= 24) wpf *= 2;
-    void (*kern)(const QcParams) = wpf == 1   ? fwbf_decode_i8_qc_kernel<1>
-                                   : wpf == 2 ? fwbf_decode_i8_qc_kernel<2>
-                                   : wpf == 4 ? fwbf_decode_i8_qc_kernel<4>
-                                              : fwbf_decode_i8_qc_kernel<8>;
+    // R = 8 pairs per lane per gather chunk when a block column's H / 32 pair
+    // groups divide by 8, else 4 (Z is a multiple of 64, so H / 32 is even)
+    const bool r8 = (P.H / 32) % 8 == 0;
+    void (*kern)(const QcParams);
+    if (r8)
+        kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<8, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<8, 2>
+             : wpf == 4 ? fwbf_decode_i8_qc_kernel<8, 4> : fwbf_decode_i8_qc_kernel<8, 8>;
+    else if ((P.H / 32) % 4 == 0)
+        kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<4, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<4, 2>
+             : wpf == 4 ? fwbf_decode_i8_qc_kernel<4, 4> : fwbf_decode_i8_qc_kernel<4, 8>;
+    else
+        kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<2, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<2, 2>
+             : wpf == 4 ? fwbf_decode_i8_qc_kernel<2, 4> : fwbf_decode_i8_qc_kernel<2, 8>;
     int per_sm = 0;
     uint32_t dyn = 0;
     cudaError_t e = cudaSuccess;

@@ -52,7 +52,7 @@ __device__ __forceinline__ void qc_pair_slot(uint32_t c, uint32_t a, uint32_t H,
 // Decodes frame f of P with a group of WPF warps (thread t of 32 * WPF); tbl
 // is the code's table blob staged in shared memory, ws the group's slice,
 // bar_id its named barrier (WPF > 1).
-template <int WPF>
+template <int R, int WPF>  // pairs per lane per gather chunk, warps per frame
 __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl, unsigned char *ws, int t, int bar_id,
                                          unsigned long long f) {
     constexpr int G = 32 * WPF;
@@ -182,30 +182,41 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
             iters = -P.max_iter;
             break;
         }
-        // gather over the column's entries, then the per-block candidates
-        for (int pj = t; pj < NB * (int)H; pj += G) {
-            const uint32_t c = div_small((uint32_t)pj, H, P.h_magic);
-            const uint32_t j = (uint32_t)pj - c * H;
-            uint32_t acc = 0u;
+        // gather over the column's entries, then the per-block candidates:
+        // chunks of 32 R consecutive pairs of one block column, R per lane
+        // (the column's entries and addresses shared by the lane's R pairs)
+        const int cpc = (int)H / (32 * R);  // chunks per block column
+        for (int ch = gw; ch < NB * cpc; ch += WPF) {
+            const uint32_t c = (uint32_t)(ch / cpc);
+            const uint32_t j0 = (uint32_t)(ch - (int)c * cpc) * 32u * R + (uint32_t)lane;
+            uint32_t acc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = 0u;
             for (uint32_t e = cptr[c]; e < cptr[c + 1]; ++e) {
                 const uint32_t ent = cent[e];
-                acc += X2[(ent >> 16) * (uint32_t)XJ + j + (ent & 0xffffu)];
-            }
-            const uint32_t SC2 = SC[pj];
-            // D_n >= 1 is necessary for E' > theta >= 0 (both halves at once)
-            const uint32_t cmask = (acc + SC2 + dfilter) & 0x80008000u;
-            if (cmask == 0u) continue;
+                const uint32_t *xb = X2 + (ent >> 16) * (uint32_t)XJ + j0 + (ent & 0xffffu);
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const uint32_t n = c * Z + j + (half ? H : 0u);
-                const int Gv = (int)((acc >> (16 * half)) & 0xffffu);
-                const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
-                const int E = (Gv + sc - bias) * 256 - aq * abs((int)q[n]);
-                if (E > tq) {
-                    const uint32_t blk = div_small(n, P.p, P.p_magic);
-                    const unsigned long long key =
-                        ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - n);
-                    atomicMax(&keys[blk], key);
+                for (int r = 0; r < R; ++r) acc[r] += xb[32 * r];
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t j = j0 + 32u * r;
+                const uint32_t SC2 = SC[c * H + j];
+                // D_n >= 1 is necessary for E' > theta >= 0 (both halves at once)
+                const uint32_t cmask = (acc[r] + SC2 + dfilter) & 0x80008000u;
+                if (cmask == 0u) continue;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const uint32_t n = c * Z + j + (half ? H : 0u);
+                    const int Gv = (int)((acc[r] >> (16 * half)) & 0xffffu);
+                    const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
+                    const int E = (Gv + sc - bias) * 256 - aq * abs((int)q[n]);
+                    if (E > tq) {
+                        const uint32_t blk = div_small(n, P.p, P.p_magic);
+                        const unsigned long long key =
+                            ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - n);
+                        atomicMax(&keys[blk], key);
+                    }
                 }
             }
         }
