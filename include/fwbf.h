@@ -96,7 +96,10 @@ int fwbf_quantize(const float *y, int8_t *q, int64_t count, void *stream);
 /*
  * FWBF on int8 channel values (Sec. III with Eq. 1 in fixed point).
  *   y          device int8 [n_frames][N], frames packed back to back (stride N
- *              bytes); the base address must be 16-byte aligned.
+ *              bytes); the base address must be 16-byte aligned.  Values lie in
+ *              [-127, 127], the range fwbf_quantize writes; for a frame holding
+ *              -128 the decisions and pass count are unspecified (the kernels
+ *              still touch no memory outside the buffers given).
  *   n_frames   >= 0 (0 queues nothing)
  *   max_iter   K_max >= 1
  *   alpha      weighting factor of Eq. 1, 0 <= alpha <= 64; it is used as
@@ -104,7 +107,7 @@ int fwbf_quantize(const float *y, int8_t *q, int64_t count, void *stream);
  *              E'_n = 256 sum (2 s_m - 1) w_{n,m} - alpha_q |q_n|, exact in int32.
  *   out_bits   device uint32 [n_frames][ceil(N/32)]
  *   out_iters  device int32 [n_frames]
- * Results are bit-identical to the definition above for every input.
+ * Results are bit-identical to the definition above for every input in that range.
  */
 int fwbf_decode(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter,
                 float alpha, uint32_t *out_bits, int32_t *out_iters, void *stream);

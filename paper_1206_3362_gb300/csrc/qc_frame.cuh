@@ -72,7 +72,7 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
     int rhalf = 0;
     const uint32_t Z = (uint32_t)P.Z, H = (uint32_t)P.H;
     const int MB = P.MB, NB = P.NB, XJ = P.XJ;
-    const int N = NB * (int)Z, M = MB * (int)Z;
+    const int N = NB * (int)Z;
     const int Nw = N >> 5;
     const int bias = 128 * P.dv + 0x4000;
     const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
@@ -100,10 +100,22 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
     }
     for (int i = t; i < NB * (int)H; i += G) SC[i] = 0x40004000u;
     group_sync<WPF>(bar_id);
-    const int8_t *q = stage + off;
+    // the staged bytes become sign-magnitude bytes sm = |q| << 1 | (q < 0),
+    // four per word (per byte: |q| = (q ^ 0xff) + 1 for q < 0, no carry
+    // across bytes since |q| <= 127); sm << 7 is the packed check-pass key
+    {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(stage);
+        for (int w = t; w < nchunks * 4; w += G) {
+            const uint32_t x = w32[w];
+            const uint32_t sg = (x >> 7) & 0x01010101u;
+            w32[w] = (((x ^ (sg * 0xffu)) + sg) << 1) | sg;
+        }
+    }
+    group_sync<WPF>(bar_id);
+    const uint8_t *sm = reinterpret_cast<const uint8_t *>(stage) + off;
     for (int w = gw; w < Nw; w += WPF) {
         const int n = (w << 5) + lane;
-        const uint32_t zb = __ballot_sync(FULL, q[n] < 0);
+        const uint32_t zb = __ballot_sync(FULL, sm[n] & 1u);
         if (lane == 0) zbits[w] = zb;
     }
 
@@ -123,13 +135,13 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
             a = a >= Z ? a - Z : a;
             uint32_t b = a + H;
             b = b >= Z ? b - Z : b;
-            const int v1 = q[cZ + a], v2 = q[cZ + b];
-            const uint32_t key = qkey(v1) | (qkey(v2) << 16) | ek;
+            const uint32_t v = (uint32_t)sm[cZ + a] | ((uint32_t)sm[cZ + b] << 16);
+            const uint32_t key = (v << 7) | ek;  // |q| << 8 | sign << 7 | entry, both halves
             k2 = vmin_u16x2(k2, vmax_u16x2(k1, key));
             k1 = vmin_u16x2(k1, key);
-            par ^= ((uint32_t)v1 & 0x80u) | (((uint32_t)v2 & 0x80u) << 16);
+            par ^= v;
         }
-        const uint32_t s_lo = (par >> 7) & 1u, s_hi = (par >> 23) & 1u;
+        const uint32_t s_lo = par & 1u, s_hi = (par >> 16) & 1u;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const uint32_t ii = i + (half ? H : 0u);
@@ -210,7 +222,7 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
                     const uint32_t n = c * Z + j + (half ? H : 0u);
                     const int Gv = (int)((acc[r] >> (16 * half)) & 0xffffu);
                     const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
-                    const int E = (Gv + sc - bias) * 256 - aq * abs((int)q[n]);
+                    const int E = (Gv + sc - bias) * 256 - aq * (int)(sm[n] >> 1);
                     if (E > tq) {
                         const uint32_t blk = div_small(n, P.p, P.p_magic);
                         const unsigned long long key =
