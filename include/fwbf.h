@@ -58,8 +58,15 @@ typedef struct {
     int32_t max_row_overlap; /* most bits any two checks share: the RC constraint
                                 of Sec. II (no two rows with two common ones)
                                 holds iff this is <= 1; the decoder works either way */
-    int32_t reserved;
+    int32_t decoder;    /* kernel fwbf_decode (and its _noalloc / _host forms)
+                           runs for this code: FWBF_DECODER_LIST, _CYCLIC or _QC */
 } fwbf_code_info;
+
+/* fwbf_code_info.decoder.  All three compute the same results (bit-identical);
+ * they differ in the layout they exploit. */
+#define FWBF_DECODER_LIST 0   /* explicit index lists, any H */
+#define FWBF_DECODER_CYCLIC 1 /* packed: H one circulant (N = M = Z, e.g. EG codes) */
+#define FWBF_DECODER_QC 2     /* packed: H blocks of Z x Z circulants, Z % 64 == 0 */
 
 /*
  * Builds a code handle from the ones of H (Sec. II: H = [h_mn], M x N).

@@ -138,7 +138,8 @@ static int launch_generic_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_fr
 }
 
 // Picks the decoder for the code: the packed cyclic kernel when H is a single
-// circulant it handles, the generic kernel otherwise.
+// circulant it handles, the packed quasi-cyclic kernel when H is made of
+// circulant blocks it handles, the generic (list) kernel otherwise.
 static int launch_i8_with_counter(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
                                   int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
                                   unsigned long long *counter, cudaStream_t s) {

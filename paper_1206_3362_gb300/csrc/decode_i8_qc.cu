@@ -129,19 +129,22 @@ int launch_decode_i8_qc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames,
     // up to 24 warps per block: 2, 4 or 8 warps per frame when fewer frames fit
     int wpf = 1;
     while (wpf < 8 && frames * wpf * 2 <= 24) wpf *= 2;
-    // R = 8 pairs per lane per gather chunk when a block column's H / 32 pair
-    // groups divide by 8, else 4 (Z is a multiple of 64, so H / 32 is even)
-    const bool r8 = (P.H / 32) % 8 == 0;
+    // R pairs per lane per gather chunk: the largest of 8, 4, 2, 1 that divides
+    // a block column's H / 32 = Z / 64 groups of 32 pairs (odd for Z = 64, 192, ...)
+    const int groups = P.H / 32;
     void (*kern)(const QcParams);
-    if (r8)
+    if (groups % 8 == 0)
         kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<8, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<8, 2>
              : wpf == 4 ? fwbf_decode_i8_qc_kernel<8, 4> : fwbf_decode_i8_qc_kernel<8, 8>;
-    else if ((P.H / 32) % 4 == 0)
+    else if (groups % 4 == 0)
         kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<4, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<4, 2>
              : wpf == 4 ? fwbf_decode_i8_qc_kernel<4, 4> : fwbf_decode_i8_qc_kernel<4, 8>;
-    else
+    else if (groups % 2 == 0)
         kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<2, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<2, 2>
              : wpf == 4 ? fwbf_decode_i8_qc_kernel<2, 4> : fwbf_decode_i8_qc_kernel<2, 8>;
+    else
+        kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<1, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<1, 2>
+             : wpf == 4 ? fwbf_decode_i8_qc_kernel<1, 4> : fwbf_decode_i8_qc_kernel<1, 8>;
     int per_sm = 0;
     uint32_t dyn = 0;
     cudaError_t e = cudaSuccess;

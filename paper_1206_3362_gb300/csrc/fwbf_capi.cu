@@ -243,7 +243,7 @@ int fwbf_code_query(fwbf_code c, fwbf_code_info *out) {
     out->n_blocks = c->B;
     out->table_bytes = (int64_t)c->table_words * 4;
     out->max_row_overlap = c->max_row_overlap;
-    out->reserved = 0;
+    out->decoder = cyclic_eligible(c) ? FWBF_DECODER_CYCLIC : qc_eligible(c) ? FWBF_DECODER_QC : FWBF_DECODER_LIST;
     return FWBF_OK;
 }
 

@@ -15,7 +15,7 @@
 //   * per pass: V'_m = (2 s_m - 1) min1_m + 128 lives in a doubled pair array
 //     per block row (X2r[k] = V'(r, k mod Z) | V'(r, (k + H) mod Z) << 16), so
 //     a bit pair gathers over its column's entries (r, t') with one aligned,
-//     conflict-free load each: D_n = G_n - 128 d_v + SC_n - 0x4000, metric
+//     conflict-free load each: D_n = G_n - 128 d_v(c) + SC_n - 0x4000, metric
 //     E' = 256 D_n - alpha_q |q_n|.
 //   * flips toggle the syndrome and keep V' and SC current with atomics; a
 //     pass without flips ends the frame (its state would repeat to K_max).
@@ -74,8 +74,6 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
     const int MB = P.MB, NB = P.NB, XJ = P.XJ;
     const int N = NB * (int)Z;
     const int Nw = N >> 5;
-    const int bias = 128 * P.dv + 0x4000;
-    const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
     const uintptr_t ybase = reinterpret_cast<uintptr_t>(P.y);
     const uintptr_t yend = ybase + (uintptr_t)(P.F * (int64_t)N);
 
@@ -201,10 +199,15 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
         for (int ch = gw; ch < NB * cpc; ch += WPF) {
             const uint32_t c = (uint32_t)(ch / cpc);
             const uint32_t j0 = (uint32_t)(ch - (int)c * cpc) * 32u * R + (uint32_t)lane;
+            // D_n = G_n - 128 d_v(c) + SC_n - 0x4000: the block column's own
+            // weight d_v(c) (block columns may differ in weight)
+            const uint32_t e0 = cptr[c], e1 = cptr[c + 1];
+            const int bias = 128 * (int)(e1 - e0) + 0x4000;
+            const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
             uint32_t acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = 0u;
-            for (uint32_t e = cptr[c]; e < cptr[c + 1]; ++e) {
+            for (uint32_t e = e0; e < e1; ++e) {
                 const uint32_t ent = cent[e];
                 const uint32_t *xb = X2 + (ent >> 16) * (uint32_t)XJ + j0 + (ent & 0xffffu);
 #pragma unroll

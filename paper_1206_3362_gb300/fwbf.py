@@ -23,6 +23,11 @@ FWBF_ECUDA = -3
 FWBF_EUNSUPPORTED = -4
 FWBF_ETIMEOUT = -5
 
+# CodeInfo.decoder: the kernel fwbf_decode runs for the code
+FWBF_DECODER_LIST = 0
+FWBF_DECODER_CYCLIC = 1
+FWBF_DECODER_QC = 2
+
 
 class FwbfError(RuntimeError):
     def __init__(self, status: int, msg: str):
@@ -40,7 +45,7 @@ class CodeInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("M", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("Z", ctypes.c_int32), ("dv_max", ctypes.c_int32), ("dc_max", ctypes.c_int32),
                 ("seg_len", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
-                ("table_bytes", ctypes.c_int64), ("max_row_overlap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("table_bytes", ctypes.c_int64), ("max_row_overlap", ctypes.c_int32), ("decoder", ctypes.c_int32)]
 
 
 _lib = None

@@ -50,6 +50,21 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name)
 
 
+def test_header_constants_match_binding():
+    """Status codes, decoder kinds and network sizes: the same values in the
+    header and in the Python binding."""
+    from paper_1206_3362_gb300 import fwbf
+
+    text = open(os.path.join(ROOT, "include", "fwbf.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (FWBF_\w+)\s+(-?\d+)", text, flags=re.M)}
+    names = [n for n in defines if re.match(r"FWBF_(OK|E[A-Z]+|DECODER_\w+)$", n)]
+    assert {"FWBF_OK", "FWBF_ETIMEOUT", "FWBF_DECODER_LIST", "FWBF_DECODER_CYCLIC", "FWBF_DECODER_QC"} <= set(names)
+    for n in names:
+        assert getattr(fwbf, n) == defines[n], n
+    assert [f[0] for f in fwbf.CodeInfo._fields_][-2:] == ["max_row_overlap", "decoder"]
+    assert ctypes.sizeof(fwbf.CodeInfo) == 56
+
+
 def test_strerror(lib):
     from paper_1206_3362_gb300 import fwbf
 

@@ -111,15 +111,20 @@ def test_other_codes(fwbf, key, p):
 
 def test_generic_kernel_warp_groups(fwbf):
     """Codes whose frames fill a block's shared memory run several warps per
-    frame in the list decoder: QC N = 16384 (8 warps, wide rows: a check's
-    edges shared by the lanes) and a random (3,6) N = 8064 code (narrow rows:
-    a lane per syndrome word), both against the oracle, with a ragged tail."""
-    from paper_1206_3362_gb300.inputs.codes import random_regular
+    frame in the list decoder: the QC N = 16384 code with its columns permuted
+    (no circulant structure left; 8 warps, wide rows: a check's edges shared by
+    the lanes) and a random (3,6) N = 8064 code (narrow rows: a lane per
+    syndrome word), both against the oracle, with a ragged tail."""
+    from paper_1206_3362_gb300.inputs.codes import ParityCheck, random_regular
 
-    h, c, y = frames("qc16384", 37, 5.5, seed=61)
+    h0, c, y = frames("qc16384", 37, 5.5, seed=61)
+    perm = np.random.default_rng(1).permutation(h0.N)
+    h = ParityCheck(N=h0.N, M=h0.M, rows=h0.rows, cols=perm[h0.cols].astype(np.int32))
+    yp = np.empty_like(y)
+    yp[:, perm] = y
     with fwbf.Code.from_parity_check(h, 32) as code:
-        assert code.info.Z == 512
-    assert_same(fwbf, h, 32, oracle.quantize(y), 30, 1.5)
+        assert code.info.Z == 1 and code.info.decoder == fwbf.FWBF_DECODER_LIST
+    assert_same(fwbf, h, 32, oracle.quantize(yp), 30, 1.5)
     h = random_regular(8064, 3, 6, seed=62)
     enc = Encoder(h)
     _, c = random_codewords(enc, 45, seed=63)
@@ -143,10 +148,73 @@ def test_generic_kernel_on_permuted_eg1023(fwbf):
 
 
 def test_circulant_structure_detected(fwbf):
-    for key, Z in (("eg1023", 1023), ("qc8192", 256), ("rand504", 1)):
+    for key, Z, dec in (("eg1023", 1023, fwbf.FWBF_DECODER_CYCLIC), ("qc8192", 256, fwbf.FWBF_DECODER_QC),
+                        ("qc16384", 512, fwbf.FWBF_DECODER_QC), ("rand504", 1, fwbf.FWBF_DECODER_LIST)):
         h = make_code(key)
         with fwbf.Code.from_parity_check(h, 31) as code:
             assert code.info.Z == Z
+            assert code.info.decoder == dec
+
+
+def _qc_from_weights(Z, base, seed):
+    """H of Z x Z blocks, block (r, c) the sum of base[r][c] distinct seeded
+    circulant permutations (0: an all-zero block)."""
+    from paper_1206_3362_gb300.inputs.codes import quasi_cyclic
+
+    rng = np.random.default_rng(seed)
+    return quasi_cyclic(Z, [[sorted(rng.choice(Z, size=w, replace=False).tolist()) for w in row] for row in base])
+
+
+def _qc_random_weights(MB, NB, seed):
+    """Irregular base matrix: block weights drawn from {0, 1, 1, 1, 2}, every
+    block row of weight >= 2."""
+    rng = np.random.default_rng(seed)
+    base = rng.choice([0, 1, 1, 1, 2], size=(MB, NB))
+    for r in range(MB):
+        while base[r].sum() < 2:
+            base[r, rng.integers(NB)] = 1
+    return base.tolist()
+
+
+# Quasi-cyclic codes the packed QC decoder takes, chosen to reach each of its
+# forms: R = 8, 4, 2, 1 pairs per lane per gather chunk (Z / 64 divisible by 8,
+# 4, 2, odd) and 1, 4 or 8 warps per frame (frames per block 24, 5-6, 2), with
+# irregular column weights, all-zero blocks, blocks of two circulants and an
+# all-zero block column (bits in no check).
+_QC_CASES = {
+    "z64_empty_col": (64, [[1, 1, 0, 2, 1, 1, 0, 1, 0], [0, 1, 1, 1, 2, 0, 1, 1, 0],
+                           [1, 0, 1, 1, 0, 1, 1, 1, 0]]),
+    "z128_weight2": (128, [[2, 1, 0, 1, 2, 1], [1, 2, 1, 1, 0, 2]]),
+    "z256_irregular": (256, "3x6"),
+    "z320_irregular": (320, "2x5"),
+    "z512_wpf2": (512, "3x8"),
+    "z192_wpf4": (192, "5x40"),
+    "z576_wpf8": (576, "4x40"),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_QC_CASES))
+def test_qc_packed_decoder(fwbf, case):
+    """The packed quasi-cyclic decoder against the oracle, bit-exact: all-zero
+    codeword under AWGN at 5.5, 6.5 and 7.5 dB (a third of the frames each:
+    frames that converge, frames that stall; valid for any H), several block
+    lengths p (1 or 4, a ragged one, N), K_max 1 and 40, alpha 0 and 1.5."""
+    Z, base = _QC_CASES[case]
+    seed = Z + len(case)
+    if isinstance(base, str):
+        MB, NB = map(int, base.split("x"))
+        base = _qc_random_weights(MB, NB, seed)
+    h = _qc_from_weights(Z, base, seed)
+    F = 11 if h.N > 10000 else 29
+    rate = max(0.3, 1.0 - h.M / h.N)
+    parts = np.array_split(np.zeros((F, h.N), dtype=np.uint8), 3)
+    y = np.concatenate([bpsk_awgn(c, e, rate, seed=seed) for c, e in zip(parts, (5.5, 6.5, 7.5))])
+    q = oracle.quantize(y)
+    p_small = 1 if h.N <= 8192 else 4  # p = 1 at N = 23040: 8 N bytes of block keys do not fit
+    for p, max_iter, alpha in ((37, 40, 1.5), (p_small, 1, 1.5), (h.N, 40, 0.0), (64, 40, 1.5)):
+        with fwbf.Code.from_parity_check(h, p) as code:
+            assert code.info.Z == Z and code.info.decoder == fwbf.FWBF_DECODER_QC
+        assert_same(fwbf, h, p, q, max_iter, alpha)
 
 
 @pytest.mark.parametrize("alpha", [0.0, 0.5, 3.0, 63.75])
