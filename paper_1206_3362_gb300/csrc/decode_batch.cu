@@ -9,9 +9,11 @@
 // tables with a bulk copy (TMA) on a fresh mbarrier, lays its warps' shared-
 // memory slices out for that code and lets each warp (or warp group) pull
 // frames from the job's counter until the job is exhausted; then the CTA moves on.
-// Per frame a warp runs the packed cyclic decoder (cyclic codes) or the
-// generic list decoder (every other code) -- the same device code as the
-// single-code kernels, so results are identical to fwbf_decode.
+// Per frame a warp (or warp group) runs the packed cyclic decoder (cyclic
+// codes), the packed quasi-cyclic decoder (codes of circulant blocks, groups
+// of 4 or 8 warps, Z a multiple of 256) or the generic list decoder (every
+// other code) -- the same device code as the single-code kernels, so results
+// are identical to fwbf_decode.
 //
 // A decode call is a memset of the counters plus one launch on the caller's
 // stream; it allocates nothing, so it can be captured in a CUDA graph.
@@ -19,15 +21,19 @@
 
 #include <vector>
 
-#include "cyclic_frame.cuh"
 #include "generic_frame.cuh"
+#include "qc_frame.cuh"
 
 namespace fwbf {
 
 __device__ int g_status_batch;
 
 enum JobKind : int { kJobGenericPlain = 0, kJobGenericCirc = 1, kJobCyclic4 = 2, kJobCyclic8 = 3, kJobCyclic2 = 4,
-                     kJobCyclic1 = 5, kJobCyclic4W2 = 6, kJobCyclic8W4 = 7, kJobCyclic4W4 = 8 };
+                     kJobCyclic1 = 5, kJobCyclic4W2 = 6, kJobCyclic8W4 = 7, kJobCyclic4W4 = 8,
+                     kJobQc8 = 9, kJobQc4 = 10 };  // QC: R pairs per lane per chunk
+
+__host__ __device__ inline bool job_is_cyclic(int kind) { return kind >= kJobCyclic4 && kind <= kJobCyclic4W4; }
+__host__ __device__ inline bool job_is_qc(int kind) { return kind >= kJobQc8; }
 
 struct BatchJob {
     int kind;
@@ -39,17 +45,19 @@ struct BatchJob {
     long long F;
     I8Params gp;
     CyclicParams cp;
+    QcParams qp;
 };
 
 constexpr int kMaxJobs = 16;
 
 // The whole job table travels as the launch's parameter block (constant
-// space, 16 x 424 bytes): the frame code reads its job's fields without
-// touching shared memory, which the decoders keep busy.
+// space, 16 jobs of under 600 bytes): the frame code reads its job's fields
+// without touching shared memory, which the decoders keep busy.
 struct BatchParams {
     BatchJob jobs[kMaxJobs];
     int n_jobs;
 };
+static_assert(sizeof(BatchParams) <= 32764, "kernel parameter block limit");
 
 // The CTA's frames of a cyclic job decoded by groups of WPF warps, R pairs
 // per lane per chunk (group g meets at named barrier 1 + g; the CTA-wide
@@ -90,6 +98,33 @@ __device__ __forceinline__ void batch_generic_groups(const BatchJob &J, const ui
         if (f >= (unsigned long long)J.F) break;
         generic_frame<PLAIN, WPF>(J.gp, tbl, ws, t, bar_id, f);
     }
+}
+
+// The same for a quasi-cyclic job (plain FWBF only).
+template <int R, int WPF>
+__device__ __forceinline__ void batch_qc_groups(const BatchJob &J, const uint32_t *tbl, unsigned char *smem,
+                                                unsigned long long *fslot) {
+    constexpr int G = 32 * WPF;
+    const int t = threadIdx.x % G, grp = threadIdx.x / G, bar_id = 1 + grp;
+    unsigned char *ws = smem + J.table_smem_bytes + grp * J.warp_bytes;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + J.qp.off_keys);
+    for (int b = t; b < J.qp.B; b += G) keys[b] = 0ull;
+    for (;;) {
+        if (t == 0) fslot[grp] = atomicAdd(J.counter, 1ull);
+        group_sync<WPF>(bar_id);
+        const unsigned long long f = fslot[grp];
+        if (f >= (unsigned long long)J.F) break;
+        qc_frame<R, WPF>(J.qp, tbl, ws, t, bar_id, f);
+    }
+}
+
+template <int WPF>
+__device__ __forceinline__ void batch_qc_dispatch(const BatchJob &J, const uint32_t *tbl, unsigned char *smem,
+                                                  unsigned long long *fslot) {
+    if (J.kind == kJobQc8)
+        batch_qc_groups<8, WPF>(J, tbl, smem, fslot);
+    else
+        batch_qc_groups<4, WPF>(J, tbl, smem, fslot);
 }
 
 // One frame of a cyclic job by one warp (plain jobs run the plain-only body).
@@ -136,14 +171,15 @@ __global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel
             __syncthreads();
             continue;
         }
-        const uint32_t words = J.kind <= kJobGenericCirc ? J.gp.table_words : J.cp.table_words;
-        const uint32_t *gtab = J.kind <= kJobGenericCirc ? J.gp.table : J.cp.table;
+        const bool qc = job_is_qc(J.kind), cyc = job_is_cyclic(J.kind);
+        const uint32_t words = qc ? J.qp.table_words : cyc ? J.cp.table_words : J.gp.table_words;
+        const uint32_t *gtab = qc ? J.qp.table : cyc ? J.cp.table : J.gp.table;
         uint32_t *st = reinterpret_cast<uint32_t *>(smem);
         if (!stage_table(st, gtab, words, &bars[t], &flag)) {
             if (threadIdx.x == 0) atomicOr(&g_status_batch, 1);
             return;
         }
-        if (J.kind >= kJobCyclic4) {
+        if (cyc) {
             for (int e = threadIdx.x; e < 128; e += blockDim.x) {  // zeros past d_c
                 d_off[e] = e < J.cp.DC ? st[J.cp.rent_off + e] & 0xffffu : 0u;
                 u_off[e] = e < J.cp.DC ? st[J.cp.cent_off + e] & 0xffffu : 0u;
@@ -158,6 +194,11 @@ __global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel
                     batch_cyclic_groups<4, 4>(J, d_off, u_off, smem, fslot);
                 else
                     batch_cyclic_groups<8, 4>(J, d_off, u_off, smem, fslot);
+            } else if (qc) {
+                if (J.wpf == 8)
+                    batch_qc_dispatch<8>(J, st, smem, fslot);
+                else
+                    batch_qc_dispatch<4>(J, st, smem, fslot);
             } else if (J.kind == kJobGenericPlain) {
                 batch_generic_dispatch<true>(J, st, smem, fslot);
             } else {
@@ -238,6 +279,14 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         BatchJob &b = hj[j];
         b = BatchJob{};
         const int aq = (int)nearbyint((double)in.alpha * 256.0);
+        // quasi-cyclic codes with Z a multiple of 256 (R = 8 or 4 pairs per lane
+        // per chunk): the packed QC decoder (groups of 4 or 8 warps) when a
+        // group fits, else (and for other Z) the list decoder
+        bool qc_ok = packed && !cyclic_eligible(c) && !in.mlp && warps_per_cta >= 4 && qc_eligible(c);
+        if (qc_ok) {
+            qc_layout(c, b.qp);
+            qc_ok = qc_R(b.qp) >= 4 && b.qp.table_smem_bytes + b.qp.warp_bytes + reserve <= (uint32_t)optin;
+        }
         if (packed && cyclic_eligible(c)) {
             cyclic_layout(c, b.cp);
             const int R = cyclic_R(c);
@@ -255,6 +304,17 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
             }
             b.table_smem_bytes = b.cp.table_smem_bytes;
             b.warp_bytes = b.cp.warp_bytes;
+        } else if (qc_ok) {
+            b.kind = qc_R(b.qp) == 8 ? kJobQc8 : kJobQc4;
+            b.qp.y = in.y;
+            b.qp.F = in.n_frames;
+            b.qp.max_iter = in.max_iter;
+            b.qp.alpha_q = aq;
+            b.qp.theta_q = 0;
+            b.qp.out_bits = in.out_bits;
+            b.qp.out_iters = in.out_iters;
+            b.table_smem_bytes = b.qp.table_smem_bytes;
+            b.warp_bytes = b.qp.warp_bytes;
         } else {
             generic_layout(c, b.gp);
             b.kind = c->Z == 1 ? kJobGenericPlain : kJobGenericCirc;
@@ -278,8 +338,11 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         // 4 warps per frame (packed decoder, R = 8) or 2 (R = 4) when H / 32
         // gives every warp a chunk; 2, 4 or 8 (list decoder)
         b.wpf = 1;
+        if (job_is_qc(b.kind) && frames > warps_per_cta / 4) frames = warps_per_cta / 4;
         const int spare = warps_per_cta / frames;
-        if (b.kind >= kJobCyclic4) {
+        if (job_is_qc(b.kind)) {
+            b.wpf = spare >= 8 ? 8 : 4;
+        } else if (job_is_cyclic(b.kind)) {
             const int ppl = b.cp.H / 32;
             b.wpf = spare >= 4 && ppl % 8 == 0 && ppl / 8 >= 4 ? 4 : spare >= 2 && ppl % 4 == 0 && ppl / 4 >= 2 ? 2 : 1;
             if (b.wpf > 1) b.kind = b.wpf == 4 ? kJobCyclic8W4 : kJobCyclic4W2;
@@ -295,7 +358,8 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
     // packed = 2: the grouped kernel (two 512-thread blocks per SM) when every
     // job can run warp groups in half an SM's shared memory: up to 8 frames per
     // block, two warps per frame (four when at most 4 frames fit, R = 4) for
-    // the packed decoder, 2, 4 or 8 for the list decoder
+    // the packed cyclic decoder, 4 or 8 (up to 4 frames) for the packed QC
+    // decoder, 2, 4 or 8 for the list decoder
     bool grouped = false;
     if (packed == 2) {
         int smem_sm = 0;
@@ -320,6 +384,9 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
                 int w = 2;
                 while (w < 8 && frames * w * 2 <= 16) w *= 2;
                 b.wpf = w;
+            } else if (job_is_qc(b.kind)) {
+                if (frames > 4) frames = 4;
+                b.wpf = frames <= 2 ? 8 : 4;
             } else {
                 const int ppl = b.cp.H / 32;
                 if (ppl % 4 != 0 || ppl / 4 < 2) {
@@ -364,6 +431,7 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         hj[j].counter = bh->d_counters + j;
         hj[j].gp.counter = hj[j].counter;
         hj[j].cp.counter = hj[j].counter;
+        hj[j].qp.counter = hj[j].counter;
         bh->params.jobs[j] = hj[j];
     }
     bh->params.n_jobs = n_jobs;

@@ -40,47 +40,6 @@ __global__ void __launch_bounds__(768, 1) fwbf_decode_i8_qc_kernel(const __grid_
     }
 }
 
-static uint32_t magic_of(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + d - 1) / d); }
-
-// Host: the code-dependent fields and the per-frame shared-memory layout.
-static void qc_layout(const fwbf_code_s *c, QcParams &P) {
-    auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
-    P.table = c->d_table;
-    P.table_words = c->table_words;
-    P.table_smem_bytes = a16(c->table_words * 4u);
-    P.rptr_off = c->rptr_off;
-    P.rent_off = c->rent_off;
-    P.cptr_off = c->cptr_off;
-    P.cent_off = c->cent_off;
-    P.Z = c->Z;
-    P.H = c->Z / 2;
-    P.MB = c->MB;
-    P.NB = c->NB;
-    P.XJ = P.Z + P.H - 1;
-    P.dv = c->dv_max;
-    P.p = c->p;
-    P.B = c->B;
-    P.p_magic = c->p_magic;
-    P.z_magic = c->z_magic;
-    P.h_magic = magic_of((uint32_t)P.H);
-    const uint32_t N = (uint32_t)c->N, M = (uint32_t)c->M;
-    uint32_t o = a16(N + 32);
-    P.off_X = o;
-    o += a16(4u * (uint32_t)(P.MB * P.XJ));
-    P.off_crec = o;
-    o += a16(4u * M);
-    P.off_SC = o;
-    o += a16(4u * (uint32_t)(P.NB * P.H));
-    P.off_s = o;
-    o += a16(M / 8u);
-    P.off_z = o;
-    o += a16(N / 8u);
-    P.off_keys = o;
-    o += a16(8u * (uint32_t)P.B);
-    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 8 warps
-    P.warp_bytes = o + 256u;
-}
-
 constexpr uint32_t kQcReserve = 1024u;  // static shared memory of the kernel
 
 // Quasi-cyclic H (several blocks, circulants of a multiple of 64) whose frame
@@ -129,17 +88,15 @@ int launch_decode_i8_qc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames,
     // up to 24 warps per block: 2, 4 or 8 warps per frame when fewer frames fit
     int wpf = 1;
     while (wpf < 8 && frames * wpf * 2 <= 24) wpf *= 2;
-    // R pairs per lane per gather chunk: the largest of 8, 4, 2, 1 that divides
-    // a block column's H / 32 = Z / 64 groups of 32 pairs (odd for Z = 64, 192, ...)
-    const int groups = P.H / 32;
+    const int R = qc_R(P);
     void (*kern)(const QcParams);
-    if (groups % 8 == 0)
+    if (R == 8)
         kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<8, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<8, 2>
              : wpf == 4 ? fwbf_decode_i8_qc_kernel<8, 4> : fwbf_decode_i8_qc_kernel<8, 8>;
-    else if (groups % 4 == 0)
+    else if (R == 4)
         kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<4, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<4, 2>
              : wpf == 4 ? fwbf_decode_i8_qc_kernel<4, 4> : fwbf_decode_i8_qc_kernel<4, 8>;
-    else if (groups % 2 == 0)
+    else if (R == 2)
         kern = wpf == 1 ? fwbf_decode_i8_qc_kernel<2, 1> : wpf == 2 ? fwbf_decode_i8_qc_kernel<2, 2>
              : wpf == 4 ? fwbf_decode_i8_qc_kernel<2, 4> : fwbf_decode_i8_qc_kernel<2, 8>;
     else

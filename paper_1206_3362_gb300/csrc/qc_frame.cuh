@@ -30,7 +30,6 @@ struct QcParams {
     uint32_t table_words, table_smem_bytes;
     uint32_t rptr_off, rent_off, cptr_off, cent_off;
     int Z, H, MB, NB, XJ;  // XJ = Z + H - 1 words of the doubled array per block row
-    int dv;                // largest column weight
     int p, B;
     uint32_t p_magic, z_magic, h_magic;
     const int8_t *y;
@@ -283,6 +282,53 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
     for (int w = t; w < Nw; w += G) __stcs(ob + w, zbits[w]);
     if (t == 0) P.out_iters[f] = iters;
     group_sync<WPF>(bar_id);
+}
+
+inline uint32_t qc_magic(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + d - 1) / d); }
+
+// Host: the code-dependent fields and the per-frame shared-memory layout.
+inline void qc_layout(const fwbf_code_s *c, QcParams &P) {
+    auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+    P.table = c->d_table;
+    P.table_words = c->table_words;
+    P.table_smem_bytes = a16(c->table_words * 4u);
+    P.rptr_off = c->rptr_off;
+    P.rent_off = c->rent_off;
+    P.cptr_off = c->cptr_off;
+    P.cent_off = c->cent_off;
+    P.Z = c->Z;
+    P.H = c->Z / 2;
+    P.MB = c->MB;
+    P.NB = c->NB;
+    P.XJ = P.Z + P.H - 1;
+    P.p = c->p;
+    P.B = c->B;
+    P.p_magic = c->p_magic;
+    P.z_magic = c->z_magic;
+    P.h_magic = qc_magic((uint32_t)P.H);
+    const uint32_t N = (uint32_t)c->N, M = (uint32_t)c->M;
+    uint32_t o = a16(N + 32);
+    P.off_X = o;
+    o += a16(4u * (uint32_t)(P.MB * P.XJ));
+    P.off_crec = o;
+    o += a16(4u * M);
+    P.off_SC = o;
+    o += a16(4u * (uint32_t)(P.NB * P.H));
+    P.off_s = o;
+    o += a16(M / 8u);
+    P.off_z = o;
+    o += a16(N / 8u);
+    P.off_keys = o;
+    o += a16(8u * (uint32_t)P.B);
+    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 8 warps
+    P.warp_bytes = o + 256u;
+}
+
+// R pairs per lane per gather chunk: the largest of 8, 4, 2, 1 that divides a
+// block column's H / 32 = Z / 64 groups of 32 pairs (odd for Z = 64, 192, ...)
+inline int qc_R(const QcParams &P) {
+    const int groups = P.H / 32;
+    return groups % 8 == 0 ? 8 : groups % 4 == 0 ? 4 : groups % 2 == 0 ? 2 : 1;
 }
 
 }  // namespace fwbf

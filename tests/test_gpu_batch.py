@@ -102,3 +102,57 @@ def test_batch_graph_replay(fwbf, jobs):
         for (b, it), (rb, ri) in zip(outs, ref):
             assert torch.equal(b, rb) and torch.equal(it, ri)
     fwbf.fwbf_batch_destroy(batch)
+
+
+def _qc_irregular(Z, MB, NB, seed):
+    """Seeded QC code with block weights from {0, 1, 1, 1, 2} (irregular
+    column weights, all-zero blocks, blocks of two circulants)."""
+    from paper_1206_3362_gb300.inputs.codes import quasi_cyclic
+
+    rng = np.random.default_rng(seed)
+    base = rng.choice([0, 1, 1, 1, 2], size=(MB, NB))
+    for r in range(MB):
+        while base[r].sum() < 2:
+            base[r, rng.integers(NB)] = 1
+    return quasi_cyclic(Z, [[sorted(rng.choice(Z, size=int(w), replace=False).tolist()) for w in row]
+                            for row in base])
+
+
+@pytest.mark.parametrize("warps,packed", [(16, 2), (16, 1), (8, 1), (4, 1)])
+def test_batch_quasi_cyclic_jobs(fwbf, warps, packed):
+    """QC jobs in the packed batch: QC N=16384 (Z=512, one to three frames per
+    CTA, groups of 8 warps), an irregular Z=256 code (groups of 4) and a Z=192
+    code (list decoder), beside EG(255); every job equals fwbf_decode, and
+    sampled frames equal the oracle."""
+    specs = [(make_code("qc16384"), 32, 23), (_qc_irregular(256, 3, 8, seed=71), 37, 41),
+             (_qc_irregular(192, 3, 9, seed=72), 32, 33), (make_code("eg255"), 16, 50)]
+    jobs = []
+    try:
+        for i, (h, p, F) in enumerate(specs):
+            parts = np.array_split(np.zeros((F, h.N), dtype=np.uint8), 3)
+            rate = max(0.3, 1.0 - h.M / h.N)
+            y = np.concatenate([bpsk_awgn(c, e, rate, seed=80 + i) for c, e in zip(parts, (5.5, 6.5, 7.5))])
+            q = oracle.quantize(y)
+            jobs.append(dict(h=h, p=p, q=q, qd=torch.from_numpy(q).cuda(), code=fwbf.Code.from_parity_check(h, p)))
+        assert [j["code"].info.decoder for j in jobs] == [fwbf.FWBF_DECODER_QC] * 3 + [fwbf.FWBF_DECODER_CYCLIC]
+        outs = [j["code"].outputs(j["qd"].shape[0]) for j in jobs]
+        spec = [(j["code"].handle, j["qd"], 40, 1.5, b, it) for j, (b, it) in zip(jobs, outs)]
+        batch = fwbf.fwbf_batch_create(spec, warps_per_cta=warps, packed=packed)
+        try:
+            fwbf.fwbf_decode_batch(batch)
+            torch.cuda.synchronize()
+            assert fwbf.fwbf_batch_status() == 0
+        finally:
+            fwbf.fwbf_batch_destroy(batch)
+        for k, (j, (b, it)) in enumerate(zip(jobs, outs)):
+            sb, si = j["code"].decode(j["qd"], 40, 1.5)
+            torch.cuda.synchronize()
+            assert np.array_equal(it.cpu().numpy(), si.cpu().numpy()), k
+            assert np.array_equal(b.cpu().numpy(), sb.cpu().numpy()), k
+            idx = np.arange(0, j["q"].shape[0], 5)[:8]
+            bo, io = oracle.fwbf_i8(j["h"], j["p"], j["q"][idx], 40, alpha=1.5)
+            assert np.array_equal(it.cpu().numpy()[idx], io), k
+            assert np.array_equal(b.cpu().numpy().view(np.uint32)[idx], bo), k
+    finally:
+        for j in jobs:
+            j["code"].close()
