@@ -195,10 +195,13 @@ __global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel
                 else
                     batch_cyclic_groups<8, 4>(J, d_off, u_off, smem, fslot);
             } else if (qc) {
-                if (J.wpf == 8)
+                if (J.wpf == 16) {
+                    if constexpr (GROUPED) batch_qc_dispatch<16>(J, st, smem, fslot);
+                } else if (J.wpf == 8) {
                     batch_qc_dispatch<8>(J, st, smem, fslot);
-                else
+                } else {
                     batch_qc_dispatch<4>(J, st, smem, fslot);
+                }
             } else if (J.kind == kJobGenericPlain) {
                 batch_generic_dispatch<true>(J, st, smem, fslot);
             } else {
@@ -358,8 +361,8 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
     // packed = 2: the grouped kernel (two 512-thread blocks per SM) when every
     // job can run warp groups in half an SM's shared memory: up to 8 frames per
     // block, two warps per frame (four when at most 4 frames fit, R = 4) for
-    // the packed cyclic decoder, 4 or 8 (up to 4 frames) for the packed QC
-    // decoder, 2, 4 or 8 for the list decoder
+    // the packed cyclic decoder, 4, 8 or 16 (up to 4 frames; 16 when one fits)
+    // for the packed QC decoder, 2, 4 or 8 for the list decoder
     bool grouped = false;
     if (packed == 2) {
         int smem_sm = 0;
@@ -387,6 +390,15 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
             } else if (job_is_qc(b.kind)) {
                 if (frames > 4) frames = 4;
                 b.wpf = frames <= 2 ? 8 : 4;
+                if (frames == 1) {  // the whole block on the one frame that fits
+                    QcParams q16 = b.qp;
+                    qc_set_wpf(q16, 16);
+                    if ((int64_t)q16.warp_bytes <= avail) {
+                        b.qp = q16;
+                        b.warp_bytes = q16.warp_bytes;
+                        b.wpf = 16;
+                    }
+                }
             } else {
                 const int ppl = b.cp.H / 32;
                 if (ppl % 4 != 0 || ppl / 4 < 2) {

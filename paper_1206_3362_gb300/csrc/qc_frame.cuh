@@ -320,9 +320,12 @@ inline void qc_layout(const fwbf_code_s *c, QcParams &P) {
     o += a16(N / 8u);
     P.off_keys = o;
     o += a16(8u * (uint32_t)P.B);
-    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 8 warps
+    P.off_red = o;  // group sums: 2 halves x 4 ints x up to 8 warps (qc_set_wpf: 16)
     P.warp_bytes = o + 256u;
 }
+
+// Sizes the frame's slice for groups of wpf warps (qc_layout assumes up to 8).
+inline void qc_set_wpf(QcParams &P, int wpf) { P.warp_bytes = P.off_red + (wpf > 8 ? 512u : 256u); }
 
 // R pairs per lane per gather chunk: the largest of 8, 4, 2, 1 that divides a
 // block column's H / 32 = Z / 64 groups of 32 pairs (odd for Z = 64, 192, ...)
