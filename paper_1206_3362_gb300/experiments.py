@@ -19,11 +19,17 @@
   one launch per code and point) on the same frames.  Frames reuse a pool of
   seeded codewords under fresh seeded noise (FWBF's outcome depends only on the
   error pattern and |y|, not on which codeword was sent).
+* ``qc``: plain FWBF (paper setting) on the quasi-cyclic N = 16384 and
+  N = 8192 codes at 4 dB: the packed quasi-cyclic decoder, and the list decoder
+  on the same code with its checks (rows) permuted -- no circulant structure
+  left, but the same metric for every bit, so the same results on the same
+  frames.  (Permuting bits would not do: the p-bit blocks follow bit order.)
 
     python -m paper_1206_3362_gb300.experiments tab1 [--frames N]
     python -m paper_1206_3362_gb300.experiments eg255 [--frames N]
     python -m paper_1206_3362_gb300.experiments scale4 [--frames N]
     python -m paper_1206_3362_gb300.experiments sweep1 [--frames N]
+    python -m paper_1206_3362_gb300.experiments qc [--frames N]
 """
 from __future__ import annotations
 
@@ -276,6 +282,51 @@ def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, ma
     return out
 
 
+QC_CODES = (("qc16384", 32), ("qc8192", 64))  # (code, block length p)
+
+
+def qc_decoders(frames: int = 1 << 16, reps: int = 3, ebn0: float = 4.0, max_iter: int = 100,
+                alpha: float = 1.5):
+    import numpy as np
+    import torch
+
+    from .inputs import Encoder, make_code
+    from .inputs.channel import random_codewords_torch
+    from .inputs.codes import ParityCheck
+
+    out = {"frames": frames, "ebn0_db": ebn0, "max_iter": max_iter, "alpha": alpha, "codes": {}}
+    for ci, (key, p) in enumerate(QC_CODES):
+        h = make_code(key)
+        enc = Encoder(h)
+        _, pool_c = random_codewords_torch(enc, 1 << 13, seed=6000 + ci, device="cuda")
+        q = _pool_frames(enc, pool_c, frames, ebn0, seed=6100 + ci, device="cuda")
+        perm = np.random.default_rng(ci).permutation(h.M)
+        hp = ParityCheck(N=h.N, M=h.M, rows=perm[h.rows].astype(np.int32), cols=h.cols)
+        row = {"N": h.N, "K": enc.K, "p": p}
+        res = {}
+        for name, hh, qq in (("packed_qc", h, q), ("list", hp, q)):
+            with fwbf.Code.from_parity_check(hh, p) as code:
+                bits, iters = code.outputs(frames)
+                fwbf.fwbf_decode(code.handle, qq, max_iter, alpha, bits, iters)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    fwbf.fwbf_decode(code.handle, qq, max_iter, alpha, bits, iters)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                res[name] = (bits, iters)
+                row[name] = {"decoder": int(code.info.decoder), "ms": ms,
+                             "gbps": frames * enc.K / (ms / 1e3) / 1e9,
+                             "failed_frac": float((iters < 0).float().mean().item())}
+        (b0, i0), (b1, i1) = res["packed_qc"], res["list"]
+        row["identical"] = bool(torch.equal(i0, i1)) and bool(torch.equal(b0, b1))
+        row["speedup"] = row["list"]["ms"] / row["packed_qc"]["ms"]
+        out["codes"][key] = row
+    return out
+
+
 def main():
     import argparse
 
@@ -284,7 +335,7 @@ def main():
     import __graft_entry__
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["tab1", "eg255", "scale4", "sweep1"])
+    ap.add_argument("what", choices=["tab1", "eg255", "scale4", "sweep1", "qc"])
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
@@ -296,6 +347,8 @@ def main():
         res = eg255(args.frames or (1 << 17))
     elif args.what == "sweep1":
         res = sweep1(args.frames or (1 << 20))
+    elif args.what == "qc":
+        res = qc_decoders(args.frames or (1 << 16))
     else:
         res = scale4(args.frames or (1 << 22))
     text = json.dumps(res, indent=1)

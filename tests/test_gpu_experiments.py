@@ -87,3 +87,16 @@ def test_sweep1_small(built):
         torch.cuda.synchronize()
     bo, io = oracle.fwbf_i8(h, 31, q.cpu().numpy(), 100, 1.5)
     assert np.array_equal(iters.cpu().numpy(), io) and np.array_equal(bits.cpu().numpy().view(np.uint32), bo)
+
+
+def test_qc_decoders_small(built):
+    """The quasi-cyclic comparison: the packed QC decoder and the list decoder
+    (same code, checks permuted) give identical results on every frame."""
+    from paper_1206_3362_gb300 import experiments, fwbf
+
+    out = experiments.qc_decoders(frames=1024, reps=1)
+    for key, row in out["codes"].items():
+        assert row["identical"], key
+        assert row["packed_qc"]["decoder"] == fwbf.FWBF_DECODER_QC, key
+        assert row["list"]["decoder"] == fwbf.FWBF_DECODER_LIST, key
+        assert row["packed_qc"]["ms"] > 0 and row["list"]["ms"] > 0
