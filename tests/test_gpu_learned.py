@@ -183,6 +183,36 @@ def test_decode_learned_replays_exactly(fwbf, key, p, F, ebn0):
     assert np.array_equal(np.where(ip >= 0, ip + k_learn, ip), it[fb])
 
 
+@pytest.mark.parametrize("key,p,F,ebn0", [("eg1023", 8, 120, 3.25), ("eg4095", 64, 48, 3.75)])
+def test_learned_schedule_is_network_output(fwbf, key, p, F, ebn0):
+    """Every (alpha_q, theta_q) a learned pass used is the network of the
+    float64 oracle evaluated on that pass's recorded features: alpha_q =
+    rne(256 clamp(o0, 0, 64)), theta_q = rne(256 clamp(16 o1, 0, 4096)).  The
+    kernel computes in float32 (an error below 1e-5 per output for these
+    weights), so each integer lies within half a unit of the exact value plus
+    256 x 1e-5 (alpha_q) or 4096 x 1e-5 (theta_q)."""
+    h, c, q = frames(key, F, ebn0, seed=45)
+    k_learn, K = 6, 60
+    net = _varied_network()
+    with fwbf.Code.from_parity_check(h, p) as code:
+        bits, iters = code.outputs(F)
+        sched = torch.full((F, k_learn, 2), -1, dtype=torch.int32, device="cuda")
+        feat = torch.full((F, k_learn, 8), np.nan, device="cuda")
+        fwbf.fwbf_decode_learned(code.handle, torch.from_numpy(q).cuda(), K, k_learn, 1.5, net.blob, bits, iters,
+                                 out_sched=sched, out_feat=feat)
+        torch.cuda.synchronize()
+    s = sched.cpu().numpy().reshape(-1, 2)
+    x = feat.cpu().numpy().reshape(-1, 8)
+    ran = s[:, 0] >= 0
+    assert ran.sum() > F and not np.isnan(x[ran]).any()
+    out, _ = mlp_ref.forward(net.master.cpu().numpy(), x[ran].astype(np.float64))
+    aq = 256.0 * np.clip(out[:, 0], 0.0, 64.0)
+    tq = 256.0 * np.clip(16.0 * out[:, 1], 0.0, 4096.0)
+    assert np.abs(s[ran, 0] - aq).max() <= 0.5 + 256 * 1e-5
+    assert np.abs(s[ran, 1] - tq).max() <= 0.5 + 4096 * 1e-5
+    assert len(np.unique(s[ran, 0])) > 3 and len(np.unique(s[ran, 1])) > 3
+
+
 def test_batched_learned_job_equals_single_code(fwbf):
     """A learned EG(4095) job (four warps per frame in the batch and alone), a
     learned EG(1023) job (one warp per frame in the batch, two alone) and a
