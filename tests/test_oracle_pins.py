@@ -195,6 +195,65 @@ def test_converged_output_is_codeword():
     assert not syn[:, ok].any() and syn[:, ~ok].any(axis=0).all()
 
 
+@pytest.mark.parametrize("key", ["eg255", "rand504", "qc8192"])
+def test_check_order_does_not_matter(key):
+    """Eq. 1 sums over the checks of a bit and the syndrome weight over all
+    checks, so numbering the checks differently changes nothing (a check index
+    leaking into a tie-break or a weight would break this)."""
+    from paper_1206_3362_gb300.inputs.codes import ParityCheck
+
+    h, c, y = _noisy(key, 6, 3.5, seed=21)
+    q = oracle.quantize(y)
+    perm = np.random.default_rng(22).permutation(h.M)
+    hp = ParityCheck(N=h.N, M=h.M, rows=perm[h.rows].astype(np.int32), cols=h.cols)
+    for p in (1, 16, h.N):
+        b0, i0 = oracle.fwbf_i8(h, p, q, 20, alpha=1.5)
+        b1, i1 = oracle.fwbf_i8(hp, p, q, 20, alpha=1.5)
+        assert np.array_equal(i0, i1) and np.array_equal(b0, b1)
+        assert (i0 != 0).any()
+
+
+def test_p1_is_bit_order_equivariant():
+    """With p = 1 every bit is its own block and flips iff its metric is
+    positive, so renumbering the bits only renumbers the result (for p > 1 the
+    blocks follow bit order and this does not hold)."""
+    from paper_1206_3362_gb300.inputs.codes import ParityCheck
+
+    h, c, y = _noisy("eg255", 8, 3.0, seed=23)
+    q = oracle.quantize(y)
+    perm = np.random.default_rng(24).permutation(h.N)  # bit n becomes bit perm[n]
+    hp = ParityCheck(N=h.N, M=h.M, rows=h.rows, cols=perm[h.cols].astype(np.int32))
+    qp = np.empty_like(q)
+    qp[:, perm] = q
+    b0, i0 = oracle.fwbf_i8(h, 1, q, 20, alpha=1.5)
+    b1, i1 = oracle.fwbf_i8(hp, 1, qp, 20, alpha=1.5)
+    assert np.array_equal(i0, i1)
+    z0, z1 = oracle.unpack_bits(b0, h.N), oracle.unpack_bits(b1, h.N)
+    assert np.array_equal(z1[:, perm], z0)
+    assert (i0 != 0).any()
+
+
+def test_bits_in_no_check_never_flip():
+    """A bit in no check has metric -alpha_q |q| <= 0 (Eq. 1 with M(n) empty),
+    so it keeps its hard decision; appended as a block of its own it leaves the
+    decoding of the other bits unchanged."""
+    from paper_1206_3362_gb300.inputs.codes import ParityCheck
+
+    h, c, y = _noisy("rand504", 10, 3.0, seed=25)  # N = 504 = 63 blocks of 8
+    q = oracle.quantize(y)
+    extra = np.random.default_rng(26).integers(-127, 128, size=(q.shape[0], 8)).astype(np.int8)
+    h2 = ParityCheck(N=h.N + 8, M=h.M, rows=h.rows, cols=h.cols)
+    q2 = np.concatenate([q, extra], axis=1)
+    for alpha in (0.0, 1.5):
+        b0, i0 = oracle.fwbf_i8(h, 8, q, 30, alpha=alpha)
+        b2, i2 = oracle.fwbf_i8(h2, 8, q2, 30, alpha=alpha)
+        assert np.array_equal(i0, i2)
+        z0, z2 = oracle.unpack_bits(b0, h.N), oracle.unpack_bits(b2, h.N + 8)
+        assert np.array_equal(z2[:, :h.N], z0)
+        assert np.array_equal(z2[:, h.N:], (extra < 0).astype(z2.dtype))
+        assert (i0 != 0).any()
+
+
 def test_max_iter_one():
     """With K_max = 1 the output is z_0 plus exactly the flips of pass 0."""
     h, c, y = _noisy("eg255", 4, 3.0, seed=5)
