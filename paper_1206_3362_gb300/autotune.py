@@ -4,9 +4,10 @@ Tuned per code, on seeded calibration frames at a chosen Eb/N0:
 
 * block length p of the partially parallel bit-choose and the weighting factor
   alpha -- both change results, so a candidate is admitted only if it is
-  FER-qualified: on the same calibration frames it decodes at least as many
-  frames to the transmitted codeword as the reference setting (the paper's
-  p and alpha);
+  FER-qualified: on the same calibration frames it has at most the frame
+  errors and at most the bit errors of the reference setting (the paper's p
+  and alpha; the bit errors decide on codes where every setting fails every
+  frame);
 * the decoder variant ("bit-packing width": the packed cyclic decoder with two
   positions per 32-bit register, or the list decoder with one), and, for a
   batch, the number of warps per CTA and whether every frame is decoded by a
@@ -94,11 +95,18 @@ def tune_code(h, enc, ebn0: float, p_ref: int, alpha_ref: float = 1.5, frames: i
             ref = r
         if log:
             log(r)
-    qualified = [r for r in results
-                 if r["frame_errors"] <= ref["frame_errors"] and r["bit_errors"] <= ref["bit_errors"]]
-    best = min(qualified, key=lambda r: r["ms"])
+    best = select_fastest_qualified(results, ref)
     return {"choice": {"p": best["p"], "alpha": best["alpha"]}, "reference": ref, "candidates": results,
             "frames": frames, "ebn0_db": ebn0}
+
+
+def select_fastest_qualified(results, ref):
+    """The fastest of the measured settings whose frame errors and bit errors
+    are both at most the reference's (the reference itself always qualifies);
+    ties in time keep the earlier entry."""
+    qualified = [r for r in results
+                 if r["frame_errors"] <= ref["frame_errors"] and r["bit_errors"] <= ref["bit_errors"]]
+    return min(qualified, key=lambda r: r["ms"])
 
 
 def tune_batch_shape(jobs, warps_candidates=(4, 8, 12, 16), packed_candidates=(2, 1, 0)):

@@ -1,0 +1,60 @@
+"""Host logic of the autotuner (no GPU): the FER qualification rule and the
+result cache."""
+import json
+import os
+
+from paper_1206_3362_gb300 import autotune
+
+
+def _r(p, alpha, fe, be, ms):
+    return {"p": p, "alpha": alpha, "frame_errors": fe, "bit_errors": be, "ms": ms}
+
+
+def test_fastest_setting_that_is_no_worse_wins():
+    ref = _r(31, 1.5, 10, 200, 5.0)
+    results = [
+        _r(1, 1.0, 9, 150, 2.0),     # better on both counts but slower than the winner
+        _r(8, 2.0, 10, 200, 1.5),    # equal errors, fastest qualified
+        _r(16, 2.0, 11, 100, 1.0),   # one more frame error: excluded despite being fastest
+        _r(4, 1.0, 8, 201, 1.2),     # one more bit error: excluded
+        ref,
+    ]
+    assert autotune.select_fastest_qualified(results, ref) is results[1]
+
+
+def test_reference_always_qualifies():
+    ref = _r(31, 1.5, 3, 40, 9.0)
+    results = [_r(8, 2.0, 4, 10, 1.0), _r(16, 1.0, 2, 41, 2.0), ref]
+    assert autotune.select_fastest_qualified(results, ref) is ref
+
+
+def test_bit_errors_decide_when_every_frame_fails():
+    """On a code beyond bit flipping's reach every setting fails every frame;
+    only settings with no more bit errors than the reference are admitted."""
+    ref = _r(32, 1.5, 100, 5000, 3.0)
+    results = [_r(8, 2.0, 100, 5200, 1.0), _r(16, 1.5, 100, 4900, 2.5), ref]
+    assert autotune.select_fastest_qualified(results, ref) is results[1]
+
+
+def test_ties_in_time_keep_the_earlier_setting():
+    ref = _r(31, 1.5, 5, 50, 2.0)
+    results = [_r(8, 1.0, 5, 50, 2.0), _r(8, 2.0, 5, 50, 2.0), ref]
+    assert autotune.select_fastest_qualified(results, ref) is results[0]
+
+
+def test_cache_round_trip(tmp_path):
+    path = os.path.join(tmp_path, "sub", "autotune.json")
+    c = autotune.Cache(path)
+    assert c.get("k") is None
+    c.put("k", {"choice": {"p": 8, "alpha": 2.0}})
+    with open(path) as f:
+        assert json.load(f) == {"k": {"choice": {"p": 8, "alpha": 2.0}}}
+    assert autotune.Cache(path).get("k") == {"choice": {"p": 8, "alpha": 2.0}}
+    assert not [n for n in os.listdir(os.path.dirname(path)) if ".tmp" in n]
+
+
+def test_cache_ignores_a_damaged_file(tmp_path):
+    path = os.path.join(tmp_path, "autotune.json")
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert autotune.Cache(path).get("k") is None
