@@ -45,7 +45,7 @@ def test_reductions_gloo_world2():
     s.bind(("127.0.0.1", 0))
     port = s.getsockname()[1]
     s.close()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a process that may already run threads
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == (3.0, 3.0) and out[1] == (3.0, 3.0)
