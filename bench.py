@@ -15,6 +15,8 @@ on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import atexit
+import datetime
 import json
 import os
 import statistics
@@ -45,7 +47,7 @@ DECODE_KERNEL = "fwbf_decode_i8_cyclic_kernel<4, 2, true>"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=WORKLOAD["frames"])
@@ -76,25 +78,78 @@ def workload_config(frames):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms from start()
+    to stop().  begin() and end() mark the timed region on the host clock; the
+    summary keeps the samples stamped inside it (every sample, and says so,
+    when none is)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
         self.tmp = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.tmp, stderr=subprocess.DEVNULL)
+            atexit.register(self._kill)  # never outlive the benchmark, even after an error
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def _kill(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        self.t1 = datetime.datetime.now()
+
+    @staticmethod
+    def parse(text):
+        """(timestamp or None, sm MHz, max sm MHz, active reasons) per row."""
+        out = []
+        for line in text.splitlines():
+            r = [x.strip() for x in line.split(",")]
+            if len(r) < 10:
+                continue
+            try:
+                sm, mx = float(r[2]), float(r[3])
+            except ValueError:
+                continue
+            try:
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f")
+            except ValueError:
+                ts = None
+            active = [n for n, v in zip(ClockSampler.REASONS, r[6:10]) if v.lower() == "active"]
+            out.append((ts, sm, mx, active))
+        return out
+
+    def summarise(self, rows):
+        window = "timed region"
+        use = rows
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if r[0] is not None and self.t0 <= r[0] <= self.t1]
+            if inside:
+                use = inside
+            else:
+                window = "whole run (no sample stamped inside the timed region)"
+        else:
+            window = "whole run"
+        reasons = sorted({n for r in use for n in r[3]})
+        return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": reasons, "samples": len(use), "window": window}
 
     def stop(self):
         if self.proc is None:
@@ -103,21 +158,9 @@ class ClockSampler:
         self.proc.wait()
         self.tmp.flush()
         self.tmp.seek(0)
-        rows = [r.split(",") for r in self.tmp.read().splitlines() if r.strip()]
+        rows = self.parse(self.tmp.read())
         os.unlink(self.tmp.name)
-        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            if len(r) < 9:
-                continue
-            for name, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return self.summarise(rows)
 
 
 def algorithmic_ops(iters, max_iter, E, N, B):
@@ -221,6 +264,8 @@ def main():
     # measured integer issue rate of this GPU (the roofline's measured denominator)
     peak_meas = fwbf.fwbf_peak_int_issue(1, 200.0, stream) / 1e12 if not args.no_peak else None
 
+    clocks = ClockSampler(local)
+    clocks.start()  # running before the timed region begins
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -228,11 +273,10 @@ def main():
     # timed region: K steps; events around every decode launch for the roofline
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     t_start.record(stream)
     for k in range(args.steps):
         fwbf.fwbf_quantize(y, q, stream)
@@ -241,6 +285,7 @@ def main():
         ev[k][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     clock_info = clocks.stop()
     if world > 1:
         dist.barrier()
@@ -342,18 +387,20 @@ def run_batched4(args):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         fwbf.fwbf_decode_batch(batch, s)
+    clocks = ClockSampler(0)
+    clocks.start()  # running before the timed region begins
     with torch.cuda.stream(s):
         for _ in range(max(3, args.warmup)):
             g.replay()
         torch.cuda.synchronize()
-        clocks = ClockSampler(0)
-        clocks.start()
+        clocks.begin()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
         for _ in range(args.steps):
             g.replay()
         e1.record(s)
     torch.cuda.synchronize()
+    clocks.end()
     clock_info = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
     assert fwbf.fwbf_batch_status() == 0
