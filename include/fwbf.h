@@ -225,16 +225,20 @@ typedef struct {
  * valid while the batch is used).
  *   warps_per_cta   1..16: warps per CTA of the launch (packed = 0 or 1)
  *   packed          1: cyclic codes use the packed two-positions-per-register
- *                   decoder; 0: every code uses the list decoder; 2: as 1,
- *                   with every frame decoded by a group of 2 or 4 warps in two
- *                   512-thread CTAs per SM when every job allows it (cyclic
- *                   codes with H / 32 divisible by 4 and at least 8; any code
- *                   of the list decoder), else as 1 (warps_per_cta is then
- *                   ignored when the grouped launch is taken).  Results are the
- *                   same for every choice.
- * Allocates the device job table and one frame counter per job (owned by the
- * handle).  Errors: FWBF_EINVAL, FWBF_EUNSUPPORTED (a code too large for one
- * warp's shared memory), FWBF_ENOMEM, FWBF_ECUDA.
+ *                   decoder, and quasi-cyclic codes with Z a multiple of 256
+ *                   (plain jobs, warps_per_cta >= 4) the packed quasi-cyclic
+ *                   decoder with 4 or 8 warps per frame; 0: every code uses the
+ *                   list decoder; 2: as 1, with every frame decoded by a group
+ *                   of warps in two 512-thread CTAs per SM when every job
+ *                   allows it (cyclic codes with H / 32 divisible by 4 and at
+ *                   least 8: 2 or 4 warps; those quasi-cyclic codes: 4, 8 or
+ *                   16; any code of the list decoder: 2, 4 or 8), else as 1
+ *                   (warps_per_cta is then ignored when the grouped launch is
+ *                   taken).  Results are the same for every choice.
+ * Allocates one device frame counter per job (owned by the handle); the job
+ * table travels with every launch as its parameter block.  Errors:
+ * FWBF_EINVAL, FWBF_EUNSUPPORTED (a code too large for one warp's shared
+ * memory), FWBF_ENOMEM, FWBF_ECUDA.
  */
 int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_per_cta,
                       int32_t packed, fwbf_batch *out);
