@@ -164,11 +164,34 @@ def _frames(y, N):
     return y.shape[0]
 
 
+def _need(t, n: int, name: str) -> None:
+    """t (a tensor, or None for an absent optional output) must hold at least
+    n elements: the kernels read or write exactly n, and nothing below the C
+    ABI can check the size behind a pointer."""
+    if t is not None and t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {n}")
+
+
+def _outputs(F: int, N: int, out_bits, out_iters) -> None:
+    _need(out_bits, F * ((N + 31) // 32), "out_bits")
+    _need(out_iters, F, "out_iters")
+
+
+def _feat(F: int, out_feat) -> int:
+    """Passes recorded by an optional out_feat [n_frames][P][8]."""
+    if out_feat is None:
+        return 0
+    if out_feat.dim() != 3 or out_feat.shape[0] < F or out_feat.shape[2] != MLP_IN:
+        raise ValueError(f"out_feat must have shape [{F}, passes, {MLP_IN}]")
+    return out_feat.shape[1]
+
+
 def fwbf_decode(code, y, max_iter: int, alpha: float, out_bits, out_iters, stream=None) -> None:
     import torch
 
     info = fwbf_code_query(code)
     F = _frames(y, info.N)
+    _outputs(F, info.N, out_bits, out_iters)
     _check(load_library().fwbf_decode(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
                                       _dev(out_bits, torch.int32, "out_bits"),
                                       _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
@@ -182,6 +205,7 @@ def fwbf_decode_noalloc(code, y, max_iter: int, alpha: float, out_bits, out_iter
 
     info = fwbf_code_query(code)
     F = _frames(y, info.N)
+    _outputs(F, info.N, out_bits, out_iters)
     _check(load_library().fwbf_decode_noalloc(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
                                               _dev(out_bits, torch.int32, "out_bits"),
                                               _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
@@ -207,6 +231,7 @@ def fwbf_decode_host(code, y_host, max_iter: int, alpha: float, bits_host, iters
 
     info = fwbf_code_query(code)
     F = _frames(y_host, info.N)
+    _outputs(F, info.N, bits_host, iters_host)
     _check(load_library().fwbf_decode_host(code, _host(y_host, torch.float32, "y_host"), F, int(max_iter),
                                            float(alpha), _host(bits_host, torch.int32, "bits_host"),
                                            _host(iters_host, torch.int32, "iters_host"), int(chunk_frames),
@@ -235,6 +260,7 @@ def fwbf_decode_lambda(code, y, max_iter: int, alpha: float, lam: int, out_bits,
 
     info = fwbf_code_query(code)
     F = _frames(y, info.N)
+    _outputs(F, info.N, out_bits, out_iters)
     _check(load_library().fwbf_decode_lambda(code, _dev(y, torch.int8, "y"), F, int(max_iter), float(alpha),
                                              int(lam), _dev(out_bits, torch.int32, "out_bits"),
                                              _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
@@ -245,6 +271,7 @@ def fwbf_decode_f32(code, y, max_iter: int, alpha: float, out_bits, out_iters, s
 
     info = fwbf_code_query(code)
     F = _frames(y, info.N)
+    _outputs(F, info.N, out_bits, out_iters)
     _check(load_library().fwbf_decode_f32(code, _dev(y, torch.float32, "y"), F, int(max_iter), float(alpha),
                                           _dev(out_bits, torch.int32, "out_bits"),
                                           _dev(out_iters, torch.int32, "out_iters"), _stream(stream)))
@@ -255,6 +282,7 @@ def fwbf_metric_f32(code, y, alpha: float, out_E, stream=None) -> None:
 
     info = fwbf_code_query(code)
     F = _frames(y, info.N)
+    _need(out_E, F * info.N, "out_E")
     _check(load_library().fwbf_metric_f32(code, _dev(y, torch.float32, "y"), F, float(alpha),
                                           _dev(out_E, torch.float32, "out_E"), _stream(stream)))
 
@@ -275,9 +303,11 @@ def fwbf_decode_sched(code, y, max_iter: int, alpha_q, theta_q, out_bits, out_it
     info = fwbf_code_query(code)
     F = _frames(y, info.N)
     stride = max_iter if alpha_q.dim() == 2 else 0
-    if alpha_q.shape != theta_q.shape or alpha_q.shape[-1] != max_iter:
+    if alpha_q.shape != theta_q.shape or alpha_q.shape[-1] != max_iter or alpha_q.dim() > 2 \
+            or (alpha_q.dim() == 2 and alpha_q.shape[0] < F):
         raise ValueError("schedules must be [n_frames][max_iter] or [max_iter]")
-    fp = out_feat.shape[1] if out_feat is not None else 0
+    _outputs(F, info.N, out_bits, out_iters)
+    fp = _feat(F, out_feat)
     _check(load_library().fwbf_decode_sched(code, _dev(y, torch.int8, "y"), F, int(max_iter),
                                             _dev(alpha_q, torch.int32, "alpha_q"), _dev(theta_q, torch.int32, "theta_q"),
                                             stride, _dev(out_bits, torch.int32, "out_bits"),
@@ -293,7 +323,10 @@ def fwbf_decode_learned(code, y, max_iter: int, k_learn: int, alpha_fallback: fl
 
     info = fwbf_code_query(code)
     F = _frames(y, info.N)
-    fp = out_feat.shape[1] if out_feat is not None else 0
+    _outputs(F, info.N, out_bits, out_iters)
+    _need(mlp_blob, MLP_BLOB_BYTES, "mlp_blob")
+    _need(out_sched, F * int(k_learn) * 2, "out_sched")
+    fp = _feat(F, out_feat)
     _check(load_library().fwbf_decode_learned(code, _dev(y, torch.int8, "y"), F, int(max_iter), int(k_learn),
                                               float(alpha_fallback), _dev(mlp_blob, torch.uint8, "mlp_blob"),
                                               _dev(out_bits, torch.int32, "out_bits"),
@@ -305,6 +338,8 @@ def fwbf_decode_learned(code, y, max_iter: int, k_learn: int, alpha_fallback: fl
 def fwbf_mlp_pack(master, blob, stream=None) -> None:
     import torch
 
+    _need(master, MLP_PARAMS, "master")
+    _need(blob, MLP_BLOB_BYTES, "blob")
     _check(load_library().fwbf_mlp_pack(_dev(master, torch.float32, "master"), _dev(blob, torch.uint8, "blob"),
                                         _stream(stream)))
 
@@ -312,6 +347,10 @@ def fwbf_mlp_pack(master, blob, stream=None) -> None:
 def fwbf_mlp_forward(blob, x, out, stream=None) -> None:
     import torch
 
+    if x.dim() != 2 or x.shape[1] != MLP_IN:
+        raise ValueError(f"x must have shape [samples, {MLP_IN}]")
+    _need(blob, MLP_BLOB_BYTES, "blob")
+    _need(out, x.shape[0] * MLP_OUT, "out")
     _check(load_library().fwbf_mlp_forward(_dev(blob, torch.uint8, "blob"), _dev(x, torch.float32, "x"), x.shape[0],
                                            _dev(out, torch.float32, "out"), _stream(stream)))
 
@@ -319,6 +358,12 @@ def fwbf_mlp_forward(blob, x, out, stream=None) -> None:
 def fwbf_mlp_grad(blob, x, target, n_total: int, grad, loss, stream=None) -> None:
     import torch
 
+    if x.dim() != 2 or x.shape[1] != MLP_IN:
+        raise ValueError(f"x must have shape [samples, {MLP_IN}]")
+    _need(blob, MLP_BLOB_BYTES, "blob")
+    _need(target, x.shape[0] * MLP_OUT, "target")
+    _need(grad, MLP_PARAMS, "grad")
+    _need(loss, 1, "loss")
     _check(load_library().fwbf_mlp_grad(_dev(blob, torch.uint8, "blob"), _dev(x, torch.float32, "x"),
                                         _dev(target, torch.float32, "target"), x.shape[0], int(n_total),
                                         _dev(grad, torch.float32, "grad"), _dev(loss, torch.float32, "loss"),
@@ -329,6 +374,9 @@ def fwbf_mlp_adam(master, blob, grad, m, v, step: int, lr: float, beta1=0.9, bet
                   stream=None) -> None:
     import torch
 
+    for t, name in ((master, "master"), (grad, "grad"), (m, "m"), (v, "v")):
+        _need(t, MLP_PARAMS, name)
+    _need(blob, MLP_BLOB_BYTES, "blob")
     _check(load_library().fwbf_mlp_adam(_dev(master, torch.float32, "master"), _dev(blob, torch.uint8, "blob"),
                                         _dev(grad, torch.float32, "grad"), _dev(m, torch.float32, "m"),
                                         _dev(v, torch.float32, "v"), int(step), float(lr), float(beta1),
@@ -347,8 +395,13 @@ def fwbf_batch_create(jobs, warps_per_cta: int = 16, packed: int = 1) -> ctypes.
             arr[i].mlp = _dev(job[6], torch.uint8, "mlp").value
             arr[i].k_learn = int(job[7])
         arr[i].code = code.value if isinstance(code, ctypes.c_void_p) else code
+        N = fwbf_code_query(code).N
+        F = _frames(y, N)
+        _outputs(F, N, bits, iters)
+        if len(job) > 6 and job[6] is not None:
+            _need(job[6], MLP_BLOB_BYTES, "mlp")
         arr[i].y = _dev(y, torch.int8, "y").value
-        arr[i].n_frames = y.shape[0]
+        arr[i].n_frames = F
         arr[i].max_iter = int(max_iter)
         arr[i].alpha = float(alpha)
         arr[i].out_bits = _dev(bits, torch.int32, "out_bits").value

@@ -144,3 +144,27 @@ def test_bounded_wait_probe_rejects_bad_arguments(lib):
     st = ctypes.c_int(0)
     assert lib.fwbf_probe_bounded_wait(65537, None, ctypes.byref(st)) == fwbf.FWBF_EINVAL
     assert lib.fwbf_probe_bounded_wait(16, None, None) == fwbf.FWBF_EINVAL
+
+
+def test_binding_refuses_short_buffers():
+    """The binding checks every buffer's size against what the kernels will
+    read or write before any call crosses the C ABI (which cannot see sizes)."""
+    import torch
+
+    from paper_1206_3362_gb300 import fwbf
+
+    F, N = 5, 1023  # 32 words of decisions per frame
+    fwbf._outputs(F, N, torch.empty((F, 32), dtype=torch.int32), torch.empty(F, dtype=torch.int32))
+    fwbf._outputs(0, N, torch.empty((0, 32), dtype=torch.int32), torch.empty(0, dtype=torch.int32))
+    with pytest.raises(ValueError, match="out_bits"):
+        fwbf._outputs(F, N, torch.empty((F, 31), dtype=torch.int32), torch.empty(F, dtype=torch.int32))
+    with pytest.raises(ValueError, match="out_iters"):
+        fwbf._outputs(F, N, torch.empty((F, 32), dtype=torch.int32), torch.empty(F - 1, dtype=torch.int32))
+    fwbf._need(None, 10, "optional")
+    with pytest.raises(ValueError, match="blob"):
+        fwbf._need(torch.empty(fwbf.MLP_BLOB_BYTES - 1, dtype=torch.uint8), fwbf.MLP_BLOB_BYTES, "blob")
+    assert fwbf._feat(F, None) == 0
+    assert fwbf._feat(F, torch.empty((F, 6, 8))) == 6
+    for bad in (torch.empty((F - 1, 6, 8)), torch.empty((F, 6, 7)), torch.empty((F, 48))):
+        with pytest.raises(ValueError, match="out_feat"):
+            fwbf._feat(F, bad)
