@@ -30,7 +30,8 @@
  *   weights      w_{n,m} is computed once, from the channel values, at
  *                initialisation.
  *   int8 path    q_n = saturate_{+-127}(round_half_even(16 y_n)), NaN -> 0;
- *                a_n = |q_n|; the metric is scaled by 256 so that
+ *                the decoders read an int8 input of -128 (outside that range)
+ *                as -127; a_n = |q_n|; the metric is scaled by 256 so that
  *                E'_n = 256 sum (2 s_m - 1) w_{n,m} - alpha_q a_n with
  *                alpha_q = round_half_even(256 alpha) is an exact integer.
  *
@@ -40,6 +41,10 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* An int8 channel value as the decoders read it: the quantiser's range is the
+ * symmetric [-127, 127], and -128 is read as -127. */
+static int32_t channel_q(int8_t v) { return v < -127 ? -127 : (int32_t)v; }
 
 #define ORACLE_OK 0
 #define ORACLE_EINVAL -1
@@ -195,8 +200,9 @@ int oracle_fwbf_i8(int N, int M, int64_t nnz, const int32_t *rows, const int32_t
         const int8_t *qf = q + f * (int64_t)N;
         /* Initialisation: z_0 and a_n */
         for (int n = 0; n < N; ++n) {
-            a[n] = qf[n] < 0 ? -(int32_t)qf[n] : (int32_t)qf[n];
-            z[n] = qf[n] < 0 ? 1 : 0;
+            const int32_t v = channel_q(qf[n]);
+            a[n] = v < 0 ? -v : v;
+            z[n] = v < 0 ? 1 : 0;
         }
         /* Initialisation: w_{n,m} = min over N(m)\n of a_i, directly */
         for (int m = 0; m < M; ++m) {
@@ -429,7 +435,7 @@ int oracle_single_flip_i8(int N, int M, int64_t nnz, const int32_t *rows, const 
     const int words = (N + 31) / 32;
     for (int64_t f = 0; f < n_frames; ++f) {
         for (int n = 0; n < N; ++n) {
-            int v = q[f * N + n];
+            int v = channel_q(q[f * N + n]);
             z[n] = v < 0;
             a[n] = v < 0 ? -v : v;
         }
@@ -512,7 +518,7 @@ int oracle_lambda_i8(int N, int M, int64_t nnz, const int32_t *rows, const int32
     }
     for (int64_t f = 0; f < n_frames; ++f) {
         for (int n = 0; n < N; ++n) {
-            int v = q[f * N + n];
+            int v = channel_q(q[f * N + n]);
             a[n] = v < 0 ? -v : v;
             z[n] = v < 0;
         }

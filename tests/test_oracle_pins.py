@@ -357,3 +357,134 @@ def test_lambda_two_errors():
         q[0, [j1, j2]] = -16
         assert oracle.lambda_i8(h, 2, q, 10, alpha=1.0)[1][0] == 1
         assert oracle.lambda_i8(h, 1, q, 10, alpha=1.0)[1][0] == 2
+
+
+# --------------------------------------------------------------------------
+# per-pass parameters (Eq. 1's alpha and Sec. III Step 2's flip threshold,
+# read per frame and pass from schedules: the path the learned form uses)
+# --------------------------------------------------------------------------
+
+def _single_error_frames(h, j, F):
+    q = np.repeat(_noiseless_q(np.zeros(h.N, dtype=np.uint8))[None], F, axis=0)
+    q[:, j] = -q[:, j]
+    return q
+
+
+def test_schedule_threshold_is_strict_per_frame_and_pass():
+    """One error at j in a noiseless EG(255,175) frame: E'_j = 4096 d_v - 16
+    alpha_q at every pass until j flips, and every other metric is negative.
+    Sec. III Step 2 flips iff E > threshold, so theta_q = E'_j - 1 flips j
+    (one pass) and theta_q = E'_j does not.  Each frame reads its own row of
+    the schedule and each pass its own entry: frame 1 is held by the
+    threshold at pass 0 and released at pass 1, frame 2 held for two passes,
+    frame 3 held at pass 0 by alpha_q = 256 d_v (E'_j = 0) and released at
+    pass 1 by alpha_q = 256 d_v - 1 (E'_j = 16)."""
+    h = make_code("eg255")
+    dv, K, j = 16, 6, 77
+    aq = 384
+    Ej = 4096 * dv - 16 * aq
+    q = _single_error_frames(h, j, 4)
+    A = np.full((4, K), aq, dtype=np.int32)
+    T = np.zeros((4, K), dtype=np.int32)
+    T[0, :] = Ej - 1
+    T[1, 0], T[1, 1:] = Ej, Ej - 1
+    T[2, :2], T[2, 2:] = Ej, Ej - 1
+    A[3, 0], A[3, 1:] = 256 * dv, 256 * dv - 1
+    bits, iters = oracle.fwbf_i8(h, 17, q, K, alpha_sched=A, theta_sched=T)
+    assert iters.tolist() == [1, 2, 3, 2]
+    assert not bits.any()
+    # held at every pass: the frame never converges
+    T[0, :] = Ej
+    bits, iters = oracle.fwbf_i8(h, 17, q[:1], K, alpha_sched=A[:1], theta_sched=T[:1])
+    assert iters[0] == -K and oracle.unpack_bits(bits, h.N)[0].sum() == 1
+
+
+def test_constant_schedule_equals_plain():
+    """A schedule holding the same alpha_q and theta_q = 0 at every pass is
+    plain FWBF (Sec. III), for a per-frame table and for one shared row."""
+    h = make_code("eg255")
+    enc = Encoder(h)
+    _, c = random_codewords(enc, 40, seed=61)
+    q = oracle.quantize(bpsk_awgn(c, 3.0, enc.rate, seed=61))
+    K = 20
+    bp, ip = oracle.fwbf_i8(h, 16, q, K, alpha=1.5)
+    A = np.full((40, K), 384, dtype=np.int32)
+    bs, is_ = oracle.fwbf_i8(h, 16, q, K, alpha_sched=A, theta_sched=np.zeros_like(A))
+    b1, i1 = oracle.fwbf_i8(h, 16, q, K, alpha_sched=A[0], theta_sched=np.zeros(K, dtype=np.int32))
+    assert (ip < 0).any() and (ip > 1).any()
+    for b, i in ((bs, is_), (b1, i1)):
+        assert np.array_equal(b, bp) and np.array_equal(i, ip)
+
+
+def test_schedule_rows_follow_their_frames():
+    """Frames decoded together with a per-frame schedule give exactly what
+    each frame gives alone with its own row, and swapping two frames together
+    with their rows swaps their results; the rows are chosen so that the
+    schedules do change the results."""
+    h = make_code("eg255")
+    enc = Encoder(h)
+    _, c = random_codewords(enc, 6, seed=62)
+    q = oracle.quantize(bpsk_awgn(c, 2.75, enc.rate, seed=62))
+    K = 12
+    rng = np.random.default_rng(63)
+    A = rng.integers(128, 1024, size=(6, K)).astype(np.int32)
+    T = (rng.integers(0, 3, size=(6, K)) * 2048).astype(np.int32)
+    bb, ib = oracle.fwbf_i8(h, 16, q, K, alpha_sched=A, theta_sched=T)
+    for f in range(6):
+        b1, i1 = oracle.fwbf_i8(h, 16, q[f:f + 1], K, alpha_sched=A[f:f + 1], theta_sched=T[f:f + 1])
+        assert np.array_equal(b1[0], bb[f]) and i1[0] == ib[f]
+    # the schedules matter: decoded under the next frame's row, frames change
+    nxt = [1, 2, 3, 4, 5, 0]
+    bx, ix = oracle.fwbf_i8(h, 16, q, K, alpha_sched=A[nxt], theta_sched=T[nxt])
+    assert ((ix != ib) | (bx != bb).any(axis=1)).sum() >= 2
+    perm = [1, 0, 2, 3, 4, 5]
+    bs, is_ = oracle.fwbf_i8(h, 16, q[perm], K, alpha_sched=A[perm], theta_sched=T[perm])
+    assert np.array_equal(bs, bb[perm]) and np.array_equal(is_, ib[perm])
+
+
+def test_schedule_change_at_pass_k_leaves_earlier_passes():
+    """A schedule that differs from the default only at pass k = 2 leaves the
+    trace of passes 0 and 1 (syndromes, metrics, flips) as plain FWBF's, and at
+    pass 2 the metric of Eq. 1 moves by exactly (alpha_q - alpha_q') |q_n|
+    (the same syndrome and weights, another weighting factor)."""
+    h = make_code("eg255")
+    enc = Encoder(h)
+    _, c = random_codewords(enc, 30, seed=64)
+    q = oracle.quantize(bpsk_awgn(c, 3.0, enc.rate, seed=64))
+    K, k = 10, 2
+    a = np.abs(q.astype(np.int64))
+    checked = 0
+    for f in range(30):
+        _, ip, tp = oracle.fwbf_i8(h, 16, q[f:f + 1], K, alpha=1.5, trace=True)
+        if not (ip[0] < 0 or ip[0] > k):
+            continue  # needs a frame that runs pass k
+        A = np.full(K, 384, dtype=np.int32)
+        T = np.zeros(K, dtype=np.int32)
+        A[k], T[k] = 640, 4096
+        _, _, ts = oracle.fwbf_i8(h, 16, q[f:f + 1], K, alpha_sched=A, theta_sched=T, trace=True)
+        for key in ("s", "E", "flip"):
+            assert np.array_equal(ts[key][:k], tp[key][:k]), key
+        assert np.array_equal(ts["s"][k], tp["s"][k])
+        assert np.array_equal(tp["E"][k] - ts["E"][k], (640 - 384) * a[f])
+        checked += 1
+    assert checked >= 5
+
+
+def test_minus_128_reads_as_minus_127():
+    """An int8 input of -128 lies outside the quantiser's symmetric range;
+    every int8 routine reads it as -127 (same decisions, passes and metrics)."""
+    h = make_code("eg255")
+    enc = Encoder(h)
+    _, c = random_codewords(enc, 12, seed=65)
+    q = oracle.quantize(bpsk_awgn(c, 3.0, enc.rate, seed=65))
+    q[np.random.default_rng(66).random(q.shape) < 0.1] = -128
+    q127 = np.maximum(q, -127).astype(np.int8)
+    assert (q == -128).sum() > 100
+    for run in (lambda x: oracle.fwbf_i8(h, 16, x, 20, alpha=1.5),
+                lambda x: oracle.single_flip_i8(h, x, 20, alpha=1.5),
+                lambda x: oracle.lambda_i8(h, 4, x, 20, alpha=1.5)):
+        r, r127 = run(q), run(q127)
+        assert all(np.array_equal(u, v) for u, v in zip(r, r127))
+    _, _, t = oracle.fwbf_i8(h, 16, q[:1], 5, alpha=1.5, trace=True)
+    _, _, t127 = oracle.fwbf_i8(h, 16, q127[:1], 5, alpha=1.5, trace=True)
+    assert np.array_equal(t["E"], t127["E"])
