@@ -103,10 +103,9 @@ int fwbf_quantize(const float *y, int8_t *q, int64_t count, void *stream);
 /*
  * FWBF on int8 channel values (Sec. III with Eq. 1 in fixed point).
  *   y          device int8 [n_frames][N], frames packed back to back (stride N
- *              bytes); the base address must be 16-byte aligned.  Values lie in
- *              [-127, 127], the range fwbf_quantize writes; for a frame holding
- *              -128 the decisions and pass count are unspecified (the kernels
- *              still touch no memory outside the buffers given).
+ *              bytes); the base address must be 16-byte aligned.  The decoder
+ *              works on the range fwbf_quantize writes, [-127, 127]: an input
+ *              of -128 is read as -127.
  *   n_frames   >= 0 (0 queues nothing)
  *   max_iter   K_max >= 1
  *   alpha      weighting factor of Eq. 1, 0 <= alpha <= 64; it is used as
@@ -299,19 +298,30 @@ int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t ma
 
 /*
  * FWBF whose pass parameters come from the learned network, with plain FWBF
- * as the fallback.  For pass k < k_learn the decoding warp evaluates the
+ * as the fallback.  For pass k < k_learn the decoding warps evaluate the
  * network on the features above: outputs (o0, o1) give alpha = o0 and
- * theta = 16 o1 (in units of the int8 metric; theta_q = rne(256 theta)),
- * clamped to [0, 64] and [0, 4096].  A frame whose syndrome is not zero after
- * k_learn passes is decoded again from its channel values by plain FWBF
- * (alpha_fallback, threshold 0, max_iter passes); its pass count is then
- * k_learn + the fallback's passes (or -max_iter if the fallback fails too).
- *   mlp          device weight blob, FWBF_MLP_BLOB_BYTES, 16-byte aligned:
- *                W1 bf16[64][8] | W2 bf16[64][64] | W3 bf16[2][64] |
+ * theta = 16 o1 (in units of the int8 metric; theta_q = 256 theta),
+ * then snapped to steps of 1/2 (alpha) and 4 (theta) and clamped to [0, 64]
+ * and [0, 4096].  A pass whose syndrome weight W_k is below 6 d_v (six times
+ * the largest column weight: about six bit errors' worth of unsatisfied
+ * checks) does not evaluate the network and uses (alpha_fallback, 0).
+ * Fallback: a frame whose syndrome is not zero after k_learn learned passes
+ * gets plain FWBF's own result for it (what fwbf_decode with alpha_fallback
+ * and max_iter gives: decisions and pass count).  If every learned pass so far
+ * used (alpha_fallback, 0), the frame's state already is plain FWBF's and
+ * decoding continues from it; otherwise the frame is decoded again from its
+ * channel values.  (A learned pass at the fallback parameters that flips
+ * nothing is treated alike at once: every later learned pass would repeat it.)
+ *   mlp          device weight blob, FWBF_MLP_BLOB_BYTES, 16-byte aligned
+ *                (written by fwbf_mlp_pack / fwbf_mlp_adam):
+ *                W1 bf16[64][8] | W2 bf16 | W3 bf16[2][64] |
  *                b1 f32[64] | b2 f32[64] | b3 f32[2]  (bytes 0, 1024, 9216,
- *                9472, 9728, 9984)
+ *                9472, 9728, 9984).  W2 (unit u, input c) is stored in 512
+ *                groups of eight: group 64 (c / 8) + u, element c % 8, so that
+ *                lanes taking consecutive units read contiguous bytes.
  *   out_sched    device int32 [n_frames][k_learn][2] or NULL: the (alpha_q,
- *                theta_q) used in every learned pass that ran
+ *                theta_q) used in every learned pass that ran (unwritten for
+ *                the passes a frame skips)
  *   out_feat, feat_passes   as fwbf_decode_sched
  */
 int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter,

@@ -12,6 +12,10 @@ namespace fwbf {
 
 constexpr int kModePlain = 0, kModeSched = 1, kModeLearned = 2;
 constexpr int kFeatures = FWBF_MLP_IN;
+// what a compiled body of the frame decoder handles (smaller bodies stay in the
+// instruction cache): plain FWBF alone; learned decoding without recording;
+// every mode (schedules, learned, feature and schedule recording)
+constexpr int kVarPlain = 0, kVarLearned = 1, kVarAll = 2;
 
 struct CyclicParams {
     const uint32_t *table;
@@ -37,6 +41,14 @@ struct CyclicParams {
     float *out_feat;      // [F][feat_passes][kFeatures] features per pass, or null
     int feat_passes;
     uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys, off_red;
+    uint32_t off_h;       // 64 floats of layer-1 outputs of the network (kModeLearned)
+    float inv_Z, inv_B;   // 1 / Z and 1 / B (features)
+    // block arg-max keys: 32-bit keys (E' << ksh | (2^ksh - 1 - offset in the
+    // block)) when every positive E' fits beside the offset, else (ksh = -1)
+    // 64-bit keys ((E' ^ 2^31) << 32 | (2^32 - 1 - n)); key_words uint32 words
+    int ksh;
+    uint32_t key_words;
+    int w_gate;           // learned passes with W below this use the fallback parameters
 };
 
 __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
@@ -108,9 +120,10 @@ __device__ __forceinline__ int flip_check(uint32_t *X2, uint32_t *SC, uint32_t r
 // group's shared-memory slice, bar_id the group's named barrier (WPF > 1).
 // The check pass and the gather split their chunks over the warps, the flips
 // their blocks; every other loop strides over the group's threads.
-// PLAIN_ONLY compiles plain FWBF alone (no schedules, network or features: a
-// smaller body for the instruction cache, 3.5 % faster on EG(1023)).
-template <int R, int WPF, bool PLAIN_ONLY = false>  // pairs per lane per chunk, warps per frame
+// VAR selects the compiled body (kVarPlain: plain FWBF alone, no schedules,
+// network or features, 3.5 % faster on EG(1023) than the full body;
+// kVarLearned: P.mode is kModeLearned and nothing is recorded; kVarAll: any mode).
+template <int R, int WPF, int VAR>  // pairs per lane per chunk, warps per frame, body
 __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32_t *d_off, const uint32_t *u_off,
                                              unsigned char *ws, int t, int bar_id, unsigned long long f) {
     constexpr int G = 32 * WPF;
@@ -124,8 +137,11 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
+    uint32_t *keys32 = reinterpret_cast<uint32_t *>(ws + P.off_keys);
+    const uint32_t kmask = P.ksh >= 0 ? (1u << P.ksh) - 1u : 0u;
     int *red = reinterpret_cast<int *>(ws + P.off_red);
     float *mlp_slot = reinterpret_cast<float *>(ws + P.off_red + 32 * WPF);  // network halves (WPF > 1)
+    float *mlp_h = reinterpret_cast<float *>(ws + P.off_h);                    // network layer 1 (learned)
     int rhalf = 0;
     const int Z = P.Z, H = P.H, DC = P.DC;
     const int Zw = (Z + 31) >> 5;
@@ -136,13 +152,17 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     const uint32_t my_u = lane < DC ? u_off[lane] : 0u;  // column offset of row position e = lane
     const int bias = 128 * DC + 0x4000;
     const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
-    const float inv_Z = 1.0f / (float)Z, inv_B = 1.0f / (float)P.B;
 
     // ---- frame load (aligned 16-byte chunks; byte loads at the buffer end)
     const uintptr_t fb = ybase + (uintptr_t)(f * (unsigned long long)Z);
     const uintptr_t a0 = fb & ~(uintptr_t)15;
     const int off = (int)(fb - a0);
     const int nchunks = (off + Z + 15) >> 4;
+    // frame statistics for the features of scheduled and learned decoding,
+    // taken from the loaded chunks (bytes outside the frame masked) and summed
+    // over the group with the check pass's syndrome weight
+    const bool stats = VAR == kVarLearned || (VAR == kVarAll && (P.mode != kModePlain || P.out_feat));
+    int sa = 0, sw = 0;  // sum of |q_n|, count of |q_n| < 8
     for (int c = t; c < nchunks; c += G) {
         const uintptr_t src = a0 + (uintptr_t)c * 16;
         uint4 v;
@@ -155,24 +175,52 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                     wv[i >> 2] |= (uint32_t)(*reinterpret_cast<const unsigned char *>(src + i)) << (8 * (i & 3));
             v = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
+        v = clamp_m127(v);
         *reinterpret_cast<uint4 *>(stage + c * 16) = v;
+        if (stats) {
+            const int lo = off - 16 * c, hi = off + Z - 16 * c;  // frame bytes of the chunk: [lo, hi)
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int l = lo - 4 * i, h = hi - 4 * i;  // frame bytes of word i: [l, h)
+                uint32_t keep = l >= 4 || h <= 0 ? 0u : 0xffffffffu;
+                if (l > 0 && l < 4) keep <<= 8 * l;
+                if (h > 0 && h < 4) keep &= 0xffffffffu >> (8 * (4 - h));
+                const uint32_t a = __vabsss4(wv[i]) & keep;  // |q| per byte (q >= -127)
+                sa += (int)__vsadu4(a, 0u);
+                sw += __popc(__vcmpltu4(a, 0x08080808u) & keep) >> 3;
+            }
+        }
+    }
+    if (stats) {
+        sa = warp_sum(sa);
+        sw = warp_sum(sw);
+        if (WPF > 1 && lane == 0) {
+            red[4 * gw] = sa;
+            red[4 * gw + 1] = sw;
+        }
     }
     group_sync<WPF>(bar_id);
     const int8_t *q = stage + off;
-    // frame statistics for the features of scheduled and learned decoding
-    float mean_a = 0.0f, weak_frac = 0.0f;
-    if (!PLAIN_ONLY && (P.mode != kModePlain || P.out_feat)) {
-        int sa = 0, sw = 0;
-        for (int n = t; n < Z; n += G) {
-            const int a = abs((int)q[n]);
-            sa += a;
-            sw += a < 8;
+    // frame-constant features in shared memory: mean |q| / 127, fraction of
+    // |q| < 8, W_0 / Z (read by every pass; written before the group's next meeting)
+    float *fstate = reinterpret_cast<float *>(ws + P.off_red + 32 * WPF + 16);
+    if (stats) {
+        if (t == 0) {
+            if (WPF > 1) {
+                sa = sw = 0;
+#pragma unroll
+                for (int w = 0; w < WPF; ++w) {
+                    sa += red[4 * w];
+                    sw += red[4 * w + 1];
+                }
+            }
+            fstate[0] = (float)sa / (127.0f * (float)Z);
+            fstate[1] = (float)sw / (float)Z;
         }
-        const int3 s3 = group_sum3<WPF>(make_int3(warp_sum(sa), warp_sum(sw), 0), red, rhalf, lane, gw, bar_id);
-        mean_a = (float)s3.x / (127.0f * (float)Z);
-        weak_frac = (float)s3.y / (float)Z;
+        rhalf = 1;  // half 0 of the group scratch held the statistics
     }
-    int iters = 0, passes_before = 0, mode = PLAIN_ONLY ? kModePlain : P.mode;
+    int iters = 0, mode = VAR == kVarPlain ? kModePlain : VAR == kVarLearned ? kModeLearned : P.mode;
     for (;;) {  // attempts: the requested mode, then plain FWBF as fallback
     for (int i = t; i < H; i += G) SC[i] = 0x40004000u;
 
@@ -241,6 +289,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         }
     }
     W = group_sum3<WPF>(make_int3(W, 0, 0), red, rhalf, lane, gw, bar_id).x;  // (meets the group if WPF > 1)
+    if (stats && t == 0) fstate[2] = (float)W * P.inv_Z;
     if constexpr (WPF == 1) __syncwarp();
 
     // the doubled array of V'_m = (2 s_m - 1) min1_m + 128, kept current
@@ -251,17 +300,23 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     group_sync<WPF>(bar_id);
 
     // ---- iterations ------------------------------------------------------
-    const int W0 = W;
     int Wprev = W, nflip_prev = 0, ncand_prev = 0;
-    bool give_up = false;  // learned passes exhausted: fall back to plain FWBF
+    bool give_up = false;   // learned passes exhausted: fall back to plain FWBF
+    bool deviated = false;  // a learned pass used parameters other than plain FWBF's
     for (int k = 0;; ++k) {
         if (W == 0) {
-            iters = passes_before + k;
+            iters = k;
             break;
         }
-        if (!PLAIN_ONLY && mode == kModeLearned && k == P.k_learn) {
-            give_up = true;
-            break;
+        if (VAR != kVarPlain && mode == kModeLearned && k == P.k_learn) {
+            // every pass so far used plain FWBF's parameters: the state is plain
+            // FWBF's after k passes, so plain decoding continues from it
+            if (!deviated) {
+                mode = kModePlain;
+            } else {
+                give_up = true;
+                break;
+            }
         }
         if (k == P.max_iter) {
             iters = -P.max_iter;
@@ -269,33 +324,40 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         }
         // weighting factor and threshold of this pass (fixed point, x256)
         int aq = P.alpha_q, tq = P.theta_q;
-        if (!PLAIN_ONLY && (mode != kModePlain || P.out_feat)) {
-            float feat[kFeatures];
-            feat[0] = (float)W * inv_Z;
-            feat[1] = (float)Wprev * inv_Z;
-            feat[2] = (float)W0 * inv_Z;
-            feat[3] = (float)k * (1.0f / 16.0f);
-            feat[4] = (float)nflip_prev * inv_B;
-            feat[5] = (float)ncand_prev * inv_Z;
-            feat[6] = mean_a;
-            feat[7] = weak_frac;
-            const int kk = passes_before + k;
-            if (P.out_feat && kk < P.feat_passes && t == 0) {
-                float *o = P.out_feat + (f * (unsigned long long)P.feat_passes + kk) * kFeatures;
-#pragma unroll
-                for (int j = 0; j < kFeatures; ++j) o[j] = feat[j];
+        bool gated = false;  // a learned pass that used the fallback parameters
+        if (VAR != kVarPlain && mode != kModePlain) {
+            if (mode == kModeLearned) gated = W < P.w_gate;
+            // features of this pass (feat[0..3], feat[4..7]), where something uses them
+            float4 fa = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fb = fa;
+            if (!gated || (VAR == kVarAll && P.out_feat)) {
+                const float4 st = *reinterpret_cast<const float4 *>(fstate);
+                fa = make_float4((float)W * P.inv_Z, (float)Wprev * P.inv_Z, st.z, (float)k * (1.0f / 16.0f));
+                fb = make_float4((float)nflip_prev * P.inv_B, (float)ncand_prev * P.inv_Z, st.x, st.y);
             }
-            if (mode == kModeSched) {
-                const long long o = (long long)f * P.sched_stride + kk;
+            if (VAR == kVarAll && P.out_feat && k < P.feat_passes && t == 0) {
+                float *o = P.out_feat + (f * (unsigned long long)P.feat_passes + k) * kFeatures;
+                o[0] = fa.x, o[1] = fa.y, o[2] = fa.z, o[3] = fa.w;
+                o[4] = fb.x, o[5] = fb.y, o[6] = fb.z, o[7] = fb.w;
+            }
+            if (VAR == kVarAll && mode == kModeSched) {
+                const long long o = (long long)f * P.sched_stride + k;
                 aq = P.sched_a[o];
                 tq = P.sched_t[o];
             } else if (mode == kModeLearned) {
-                float al, th;
-                mlp_eval<WPF>(P.mlp, feat, lane, gw, mlp_slot, bar_id, al, th);
-                th *= 16.0f;
-                aq = __float2int_rn(fminf(fmaxf(al, 0.0f), 64.0f) * 256.0f);
-                tq = __float2int_rn(fminf(fmaxf(th, 0.0f), 4096.0f) * 256.0f);
-                if (P.out_sched && t == 0) {
+                if (!gated) {
+                    const float2 o = mlp_eval<WPF>(P.mlp, fa, fb, lane, gw, mlp_h, mlp_slot, bar_id);
+                    const float al = o.x, th = o.y;
+                    // the layer-1 outputs may share the (idle, all-zero) key array:
+                    // clear them, and meet, before this pass's keys are written
+                    if (WPF == 1 || gw < 2) mlp_h[32 * gw + lane] = 0.0f;
+                    if constexpr (WPF == 1) mlp_h[32 + lane] = 0.0f;
+                    group_sync<WPF>(bar_id);
+                    // alpha in steps of 1/2 in [0, 64], theta = 16 o1 in steps of 4 in [0, 4096]
+                    aq = 128 * __float2int_rn(fminf(fmaxf(al, 0.0f), 64.0f) * 2.0f);
+                    tq = 1024 * __float2int_rn(fminf(fmaxf(th * 4.0f, 0.0f), 1024.0f));
+                    deviated |= aq != P.alpha_q || tq != 0;
+                }
+                if (VAR == kVarAll && P.out_sched && t == 0) {
                     const unsigned long long o = (f * (unsigned long long)P.k_learn + k) * 2;
                     P.out_sched[o] = aq;
                     P.out_sched[o + 1] = tq;
@@ -333,7 +395,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                 uint32_t cmask = (G2 + SC2 + dfilter) & 0x80008000u;
                 if (i + H >= Z) cmask &= 0x8000u;  // the duplicated position
                 if (cmask == 0u) continue;
-                if (!PLAIN_ONLY) ncand += __popc(cmask);  // a feature of the next pass
+                if (VAR != kVarPlain) ncand += __popc(cmask);  // a feature of the next pass
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     const int n = i + half * H;
@@ -341,11 +403,16 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                     const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
                     const int a = abs((int)q[n < Z ? n : 0]);
                     const int E = (Gv + sc - bias) * 256 - aq * a;
-                    if (E > tq && n < Z) {
+                    if (E > tq && n < Z) {  // E >= 1: a 32-bit key is never 0
                         const uint32_t blk = div_small((uint32_t)n, P.p, P.p_magic);
-                        const unsigned long long key =
-                            ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) | (0xffffffffu - (uint32_t)n);
-                        atomicMax(&keys[blk], key);
+                        if (P.ksh >= 0) {
+                            const uint32_t off = (uint32_t)n - blk * (uint32_t)P.p;
+                            atomicMax(&keys32[blk], ((uint32_t)E << P.ksh) | (kmask - off));
+                        } else {
+                            const unsigned long long key = ((unsigned long long)((uint32_t)E ^ 0x80000000u) << 32) |
+                                                           (0xffffffffu - (uint32_t)n);
+                            atomicMax(&keys[blk], key);
+                        }
                     }
                 }
             }
@@ -358,14 +425,23 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         int dW = 0, nflip = 0;
         for (int b0 = 0; b0 < P.B; b0 += G) {
             const int b = b0 + WPF * lane + gw;
-            unsigned long long key = 0ull;
+            bool has = false;
+            uint32_t nmine = 0u;
             if (b < P.B) {
-                key = keys[b];
-                if (key) keys[b] = 0ull;
+                if (P.ksh >= 0) {
+                    const uint32_t key = keys32[b];
+                    has = key != 0u;
+                    if (has) keys32[b] = 0u;
+                    nmine = (uint32_t)b * (uint32_t)P.p + (kmask - (key & kmask));
+                } else {
+                    const unsigned long long key = keys[b];
+                    has = key != 0ull;
+                    if (has) keys[b] = 0ull;
+                    nmine = 0xffffffffu - (uint32_t)key;
+                }
             }
-            const uint32_t nmine = 0xffffffffu - (uint32_t)key;
-            if (key) atomicXor(&zbits[nmine >> 5], 1u << (nmine & 31));
-            uint32_t pend = __ballot_sync(FULL, key != 0ull);
+            if (has) atomicXor(&zbits[nmine >> 5], 1u << (nmine & 31));
+            uint32_t pend = __ballot_sync(FULL, has);
             nflip += __popc(pend);
             while (pend) {
                 const int s0 = __ffs(pend) - 1;
@@ -400,10 +476,20 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
             iters = -P.max_iter;
             break;
         }
+        if (VAR != kVarPlain && nflip == 0 && gated) {
+            // W is unchanged, so every later learned pass is gated too and repeats
+            // this one: plain FWBF's fixed point if no pass deviated (and so its
+            // result), else the frame goes to the fallback now, as at k_learn
+            if (!deviated) {
+                iters = -P.max_iter;
+                break;
+            }
+            give_up = true;
+            break;
+        }
     }
     if (!give_up) break;
-    passes_before = P.k_learn;
-    mode = kModePlain;
+    mode = kModePlain;  // plain FWBF from the channel values; its result is the frame's
     }  // attempts
 
     uint32_t *ob = P.out_bits + f * (unsigned long long)Zw;
@@ -416,10 +502,17 @@ bool cyclic_eligible(const fwbf_code_s *c);
 
 // Host: fills the code-dependent fields and the per-warp shared-memory layout.
 // bytes of a frame's group scratch for wpf warps (the last item of the slice)
-inline uint32_t cyclic_red_bytes(int wpf) { return (32u * (uint32_t)wpf + 16u + 15u) & ~15u; }
+// (2 x 4 ints per warp of group sums, 4 floats of network halves, 4 floats of
+// frame-constant features)
+inline uint32_t cyclic_red_bytes(int wpf) { return 32u * (uint32_t)wpf + 32u; }
 
-// Sizes the frame's slice for groups of wpf warps (cyclic_layout assumes 4).
-inline void cyclic_set_wpf(CyclicParams &P, int wpf) { P.warp_bytes = P.off_red + cyclic_red_bytes(wpf); }
+// Sizes the frame's slice for groups of wpf warps (cyclic_layout assumes 4);
+// learned decoding adds the network's 64 layer-1 outputs (P.mode must be set).
+inline void cyclic_set_wpf(CyclicParams &P, int wpf) {
+    const bool in_keys = 4u * P.key_words >= 256u;  // the key array is all zero between passes
+    P.off_h = in_keys ? P.off_keys : P.off_red + cyclic_red_bytes(wpf);
+    P.warp_bytes = P.off_red + cyclic_red_bytes(wpf) + (P.mode == kModeLearned && !in_keys ? 256u : 0u);
+}
 
 inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
     auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
@@ -433,6 +526,8 @@ inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
     P.p = c->p;
     P.B = c->B;
     P.p_magic = c->p_magic;
+    P.inv_Z = 1.0f / (float)c->Z;
+    P.inv_B = 1.0f / (float)c->B;
     const uint32_t Z = c->Z, H = P.H;
     uint32_t o = a16(Z + 32);
     P.off_X = o;
@@ -446,9 +541,20 @@ inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
     P.off_z = o;
     o += a16(4 * ((Z + 31) / 32));
     P.off_keys = o;
-    o += a16(8 * (uint32_t)c->B);
+    {
+        int sh = 0;
+        while ((1 << sh) < c->p) ++sh;
+        const uint64_t emax = 256ull * 127ull * (uint64_t)c->dv_max;  // largest positive E'
+        P.ksh = (emax << sh) < (1ull << 32) ? sh : -1;
+        P.key_words = (uint32_t)c->B * (P.ksh >= 0 ? 1u : 2u);
+        // learned passes with fewer unsatisfied checks than about six bit errors
+        // make use the fallback parameters (98 % of such passes are labelled
+        // with them on EG(1023,781) at 3.0-4.5 dB)
+        P.w_gate = 6 * c->dv_max;
+    }
+    o += a16(4 * P.key_words);
     P.off_red = o;  // group sums: 2 halves x 4 ints per warp of the group; then 4 floats for the network
-    P.warp_bytes = o + cyclic_red_bytes(4);
+    cyclic_set_wpf(P, 4);
     P.table_smem_bytes = a16(c->table_words * 4u);
 }
 

@@ -68,17 +68,17 @@ __device__ __forceinline__ void batch_cyclic_groups(const BatchJob &J, const uin
     constexpr int G = 32 * WPF;
     const int t = threadIdx.x % G, grp = threadIdx.x / G, bar_id = 1 + grp;
     unsigned char *ws = smem + J.table_smem_bytes + grp * J.warp_bytes;
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + J.cp.off_keys);
-    for (int b = t; b < J.cp.B; b += G) keys[b] = 0ull;
+    uint32_t *keys = reinterpret_cast<uint32_t *>(ws + J.cp.off_keys);
+    for (uint32_t b = t; b < J.cp.key_words; b += G) keys[b] = 0u;
     for (;;) {
         if (t == 0) fslot[grp] = atomicAdd(J.counter, 1ull);
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];
         if (f >= (unsigned long long)J.F) break;
         if (J.cp.mode == kModePlain)
-            cyclic_frame<R, WPF, true>(J.cp, d_off, u_off, ws, t, bar_id, f);
+            cyclic_frame<R, WPF, kVarPlain>(J.cp, d_off, u_off, ws, t, bar_id, f);
         else
-            cyclic_frame<R, WPF, false>(J.cp, d_off, u_off, ws, t, bar_id, f);
+            cyclic_frame<R, WPF, kVarLearned>(J.cp, d_off, u_off, ws, t, bar_id, f);
     }
 }
 
@@ -127,14 +127,15 @@ __device__ __forceinline__ void batch_qc_dispatch(const BatchJob &J, const uint3
         batch_qc_groups<4, WPF>(J, tbl, smem, fslot);
 }
 
-// One frame of a cyclic job by one warp (plain jobs run the plain-only body).
+// One frame of a cyclic job by one warp (plain jobs run the plain-only body,
+// learned jobs the learned body: batch jobs record nothing).
 template <int R>
 __device__ __forceinline__ void cyclic_frame_job(const BatchJob &J, const uint32_t *d_off, const uint32_t *u_off,
                                                  unsigned char *ws, int lane, unsigned long long f) {
     if (J.cp.mode == kModePlain)
-        cyclic_frame<R, 1, true>(J.cp, d_off, u_off, ws, lane, 0, f);
+        cyclic_frame<R, 1, kVarPlain>(J.cp, d_off, u_off, ws, lane, 0, f);
     else
-        cyclic_frame<R, 1, false>(J.cp, d_off, u_off, ws, lane, 0, f);
+        cyclic_frame<R, 1, kVarLearned>(J.cp, d_off, u_off, ws, lane, 0, f);
 }
 
 template <bool PLAIN>
@@ -150,7 +151,10 @@ __device__ __forceinline__ void batch_generic_dispatch(const BatchJob &J, const 
 
 // GROUPED: every job runs warp groups (two blocks of 512 threads per SM, 64
 // registers); otherwise any mix of one-warp and group jobs (one block per SM).
-template <bool GROUPED>
+// CYCLIC_ONLY (grouped launches whose jobs are all cyclic codes): only the
+// cyclic decoder bodies are compiled in, a smaller kernel for the instruction
+// cache and the register allocator.
+template <bool GROUPED, bool CYCLIC_ONLY = false>
 __global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bars[kMaxJobs];
@@ -194,6 +198,8 @@ __global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel
                     batch_cyclic_groups<4, 4>(J, d_off, u_off, smem, fslot);
                 else
                     batch_cyclic_groups<8, 4>(J, d_off, u_off, smem, fslot);
+            } else if constexpr (CYCLIC_ONLY) {
+                // (no other job kind in this launch)
             } else if (qc) {
                 if (J.wpf == 16) {
                     if constexpr (GROUPED) batch_qc_dispatch<16>(J, st, smem, fslot);
@@ -209,10 +215,12 @@ __global__ void __launch_bounds__(512, GROUPED ? 2 : 1) fwbf_decode_batch_kernel
             }
         } else if (!GROUPED && warp < J.warps) {
             unsigned char *ws = smem + J.table_smem_bytes + warp * J.warp_bytes;
-            const int B = J.kind <= kJobGenericCirc ? J.gp.nkeys : J.cp.B;
+            // key array in uint32 words: 64-bit keys in the list decoder, 32- or
+            // 64-bit keys in the cyclic decoder
+            const uint32_t kw = J.kind <= kJobGenericCirc ? 2u * (uint32_t)J.gp.nkeys : J.cp.key_words;
             const uint32_t off_keys = J.kind <= kJobGenericCirc ? J.gp.off_keys : J.cp.off_keys;
-            unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + off_keys);
-            for (int b = lane; b < B; b += 32) keys[b] = 0ull;
+            uint32_t *keys = reinterpret_cast<uint32_t *>(ws + off_keys);
+            for (uint32_t b = lane; b < kw; b += 32) keys[b] = 0u;
             __syncwarp();
             for (;;) {
                 unsigned long long f = 0;
@@ -240,6 +248,7 @@ using namespace fwbf;
 struct fwbf_batch_s {
     int n_jobs = 0;
     bool grouped = false;
+    bool cyclic_only = false;  // grouped launch of cyclic jobs only
     BatchParams params{};
     unsigned long long *d_counters = nullptr;
     int blocks = 0, threads = 0;
@@ -291,6 +300,11 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
             qc_ok = qc_R(b.qp) >= 4 && b.qp.table_smem_bytes + b.qp.warp_bytes + reserve <= (uint32_t)optin;
         }
         if (packed && cyclic_eligible(c)) {
+            if (in.mlp) {  // (before the layout: a learned frame's slice holds the network's layer 1)
+                b.cp.mode = kModeLearned;
+                b.cp.mlp = static_cast<const unsigned char *>(in.mlp);
+                b.cp.k_learn = in.k_learn;
+            }
             cyclic_layout(c, b.cp);
             const int R = cyclic_R(c);
             b.kind = R == 8 ? kJobCyclic8 : R == 4 ? kJobCyclic4 : R == 2 ? kJobCyclic2 : kJobCyclic1;
@@ -300,11 +314,6 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
             b.cp.alpha_q = aq;
             b.cp.out_bits = in.out_bits;
             b.cp.out_iters = in.out_iters;
-            if (in.mlp) {
-                b.cp.mode = 2;
-                b.cp.mlp = static_cast<const unsigned char *>(in.mlp);
-                b.cp.k_learn = in.k_learn;
-            }
             b.table_smem_bytes = b.cp.table_smem_bytes;
             b.warp_bytes = b.cp.warp_bytes;
         } else if (qc_ok) {
@@ -447,7 +456,12 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         bh->params.jobs[j] = hj[j];
     }
     bh->params.n_jobs = n_jobs;
-    void (*kern)(const BatchParams) = grouped ? fwbf_decode_batch_kernel<true> : fwbf_decode_batch_kernel<false>;
+    bool cyclic_only = grouped;
+    for (int j = 0; j < n_jobs; ++j) cyclic_only = cyclic_only && job_is_cyclic(hj[j].kind);
+    bh->cyclic_only = cyclic_only;
+    void (*kern)(const BatchParams) = cyclic_only ? fwbf_decode_batch_kernel<true, true>
+                                    : grouped     ? fwbf_decode_batch_kernel<true, false>
+                                                  : fwbf_decode_batch_kernel<false, false>;
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int per_sm = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bh->threads, dyn);
@@ -466,10 +480,12 @@ int fwbf_decode_batch(fwbf_batch b, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * b->n_jobs, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(batch counters)");
-    if (b->grouped)
-        fwbf_decode_batch_kernel<true><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
+    if (b->cyclic_only)
+        fwbf_decode_batch_kernel<true, true><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
+    else if (b->grouped)
+        fwbf_decode_batch_kernel<true, false><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
     else
-        fwbf_decode_batch_kernel<false><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
+        fwbf_decode_batch_kernel<false, false><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
     e = cudaGetLastError();
     return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "decode_batch launch");
 }

@@ -34,7 +34,7 @@ namespace fwbf {
 
 __device__ int g_status_i8_cyclic;
 
-template <int R, int WPF, bool PLAIN_ONLY>  // pairs per lane per chunk, warps per frame, plain FWBF alone
+template <int R, int WPF, int VAR>  // pairs per lane per chunk, warps per frame, body (kVar*)
 __global__ void __launch_bounds__(512, WPF == 2 ? 2 : 1) fwbf_decode_i8_cyclic_kernel(const CyclicParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint64_t bar;
@@ -60,15 +60,27 @@ __global__ void __launch_bounds__(512, WPF == 2 ? 2 : 1) fwbf_decode_i8_cyclic_k
     const int grp = threadIdx.x / G;
     const int bar_id = 1 + grp;
     unsigned char *ws = smem + P.table_smem_bytes + grp * P.warp_bytes;
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
-    for (int b = t; b < P.B; b += G) keys[b] = 0ull;
+    uint32_t *keys = reinterpret_cast<uint32_t *>(ws + P.off_keys);
+    for (uint32_t b = t; b < P.key_words; b += G) keys[b] = 0u;
     for (;;) {
         if (t == 0) fslot[grp] = atomicAdd(P.counter, 1ull);
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];  // rewritten only after the frame's last meeting
         if (f >= (unsigned long long)P.F) break;
-        cyclic_frame<R, WPF, PLAIN_ONLY>(P, d_off, u_off, ws, t, bar_id, f);
+        cyclic_frame<R, WPF, VAR>(P, d_off, u_off, ws, t, bar_id, f);
     }
+}
+
+template <int WPF, int VAR>
+static void (*cyclic_kernel_r(int R))(const CyclicParams) {
+    return R == 8 ? fwbf_decode_i8_cyclic_kernel<8, WPF, VAR> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, WPF, VAR>
+         : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, WPF, VAR> : fwbf_decode_i8_cyclic_kernel<1, WPF, VAR>;
+}
+
+template <int WPF>
+static void (*cyclic_kernel_for(int R, int var))(const CyclicParams) {
+    return var == kVarPlain ? cyclic_kernel_r<WPF, kVarPlain>(R)
+         : var == kVarLearned ? cyclic_kernel_r<WPF, kVarLearned>(R) : cyclic_kernel_r<WPF, kVarAll>(R);
 }
 
 bool cyclic_eligible(const fwbf_code_s *c) {
@@ -130,20 +142,9 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
     cyclic_set_wpf(P, wpf);
     int frames = wpf == 2 ? (fmax >= 16 ? 8 : fmax / 2) : (fmax < 4 ? fmax : 4);
     const int R = cyclic_R(c, wpf);
-    const bool plain = P.mode == kModePlain && !P.out_feat;
-    void (*kern)(const CyclicParams);
-    if (wpf == 2 && plain)
-        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 2, true> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 2, true>
-             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 2, true> : fwbf_decode_i8_cyclic_kernel<1, 2, true>;
-    else if (wpf == 2)
-        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 2, false> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 2, false>
-             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 2, false> : fwbf_decode_i8_cyclic_kernel<1, 2, false>;
-    else if (plain)
-        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 4, true> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 4, true>
-             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 4, true> : fwbf_decode_i8_cyclic_kernel<1, 4, true>;
-    else
-        kern = R == 8 ? fwbf_decode_i8_cyclic_kernel<8, 4, false> : R == 4 ? fwbf_decode_i8_cyclic_kernel<4, 4, false>
-             : R == 2 ? fwbf_decode_i8_cyclic_kernel<2, 4, false> : fwbf_decode_i8_cyclic_kernel<1, 4, false>;
+    const int var = P.mode == kModePlain && !P.out_feat ? kVarPlain
+                  : P.mode == kModeLearned && !P.out_feat && !P.out_sched ? kVarLearned : kVarAll;
+    void (*kern)(const CyclicParams) = wpf == 2 ? cyclic_kernel_for<2>(R, var) : cyclic_kernel_for<4>(R, var);
     int per_sm = 0;
     uint32_t dyn = 0;
     cudaError_t e = cudaSuccess;

@@ -88,6 +88,11 @@ __device__ __forceinline__ bool stage_table(uint32_t *dst, const uint32_t *src, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // The region may have been read and written through the generic proxy
+        // (a previous job's frame slices and tables); the barrier above orders
+        // those accesses before this thread, and the fence orders them before
+        // the bulk copies (async proxy) that overwrite the region.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, bytes);
         for (uint32_t off = 0; off < bytes; off += kBulkChunk) {
             uint32_t n = bytes - off < kBulkChunk ? bytes - off : kBulkChunk;
@@ -105,6 +110,13 @@ __device__ __forceinline__ bool stage_table(uint32_t *dst, const uint32_t *src, 
 }
 
 __device__ __forceinline__ int warp_sum(int v) { return __reduce_add_sync(FULL, v); }
+
+// Sixteen int8 channel values with -128 replaced by -127: the decoders take
+// int8 values in the quantiser's symmetric range, and -128 decodes as -127.
+__device__ __forceinline__ uint4 clamp_m127(uint4 v) {
+    const uint32_t m = 0x81818181u;  // -127 in every byte
+    return make_uint4(__vmaxs4(v.x, m), __vmaxs4(v.y, m), __vmaxs4(v.z, m), __vmaxs4(v.w, m));
+}
 
 // The WPF warps that decode one frame meet here: the warp itself, or a named
 // barrier (id bar_id, WPF * 32 threads) that also orders their shared memory.

@@ -104,7 +104,7 @@ __device__ __forceinline__ void generic_frame(const I8Params &P, const uint32_t 
                     wv[i >> 2] |= (uint32_t)(*reinterpret_cast<const unsigned char *>(src + i)) << (8 * (i & 3));
             v = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
-        *reinterpret_cast<uint4 *>(stage + c * 16) = v;
+        *reinterpret_cast<uint4 *>(stage + c * 16) = clamp_m127(v);  // -128 decodes as -127
     }
     for (int n = t; n < N; n += G) T[n] = 0u;
     group_sync<WPF>(bar_id);

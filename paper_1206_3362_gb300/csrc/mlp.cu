@@ -17,8 +17,9 @@ namespace fwbf {
 constexpr int kIn = FWBF_MLP_IN, kHid = FWBF_MLP_HIDDEN, kOut = FWBF_MLP_OUT;
 constexpr int kSamples = 32;  // samples per block of the gradient kernel
 
-__device__ __forceinline__ float blob_w(const unsigned char *blob, int off_bytes, int idx) {
-    const uint16_t h = reinterpret_cast<const uint16_t *>(blob + off_bytes)[idx];
+// master weight i (i < kPB1) as the blob holds it (bf16, widened)
+__device__ __forceinline__ float blob_w(const unsigned char *blob, int i) {
+    const uint16_t h = reinterpret_cast<const uint16_t *>(blob)[mlp_blob_index(i)];
     return __uint_as_float((uint32_t)h << 16);
 }
 
@@ -29,7 +30,7 @@ __global__ void mlp_pack_kernel(const float *__restrict__ master, unsigned char 
         const float v = master[i];
         if (i < kPB1) {
             const uint16_t h = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-            reinterpret_cast<uint16_t *>(blob)[i] = h;  // W1, W2, W3 are contiguous from offset 0
+            reinterpret_cast<uint16_t *>(blob)[mlp_blob_index(i)] = h;  // W1, W2, W3 from offset 0
         } else {
             reinterpret_cast<float *>(blob + kMlpB1)[i - kPB1] = v;  // b1, b2, b3 contiguous
         }
@@ -48,15 +49,15 @@ __global__ void mlp_forward_kernel(const unsigned char *__restrict__ blob, const
     const float *b3 = reinterpret_cast<const float *>(blob + kMlpB3);
     for (int j = 0; j < kHid; ++j) {
         float a = b1[j];
-        for (int i = 0; i < kIn; ++i) a = fmaf(blob_w(blob, kMlpW1, j * kIn + i), in[i], a);
+        for (int i = 0; i < kIn; ++i) a = fmaf(blob_w(blob, kPW1 + j * kIn + i), in[i], a);
         h1[j] = fmaxf(a, 0.0f);
     }
     float o[kOut] = {b3[0], b3[1]};
     for (int j = 0; j < kHid; ++j) {
         float a = b2[j];
-        for (int i = 0; i < kHid; ++i) a = fmaf(blob_w(blob, kMlpW2, j * kHid + i), h1[i], a);
+        for (int i = 0; i < kHid; ++i) a = fmaf(blob_w(blob, kPW2 + j * kHid + i), h1[i], a);
         a = fmaxf(a, 0.0f);
-        for (int k = 0; k < kOut; ++k) o[k] = fmaf(blob_w(blob, kMlpW3, k * kHid + j), a, o[k]);
+        for (int k = 0; k < kOut; ++k) o[k] = fmaf(blob_w(blob, kPW3 + k * kHid + j), a, o[k]);
     }
     for (int k = 0; k < kOut; ++k) out[s * kOut + k] = o[k];
 }
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(256) mlp_grad_kernel(const unsigned char *__re
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t s0 = blockIdx.x * (int64_t)kSamples;
     const int ns = (int)min((int64_t)kSamples, n - s0);
-    for (int i = tid; i < kHid * kIn; i += nt) W1[i] = blob_w(blob, kMlpW1, i);
-    for (int i = tid; i < kHid * kHid; i += nt) W2[i] = blob_w(blob, kMlpW2, i);
-    for (int i = tid; i < kOut * kHid; i += nt) W3[i] = blob_w(blob, kMlpW3, i);
+    for (int i = tid; i < kHid * kIn; i += nt) W1[i] = blob_w(blob, kPW1 + i);
+    for (int i = tid; i < kHid * kHid; i += nt) W2[i] = blob_w(blob, kPW2 + i);
+    for (int i = tid; i < kOut * kHid; i += nt) W3[i] = blob_w(blob, kPW3 + i);
     for (int i = tid; i < kHid; i += nt) {
         B1[i] = reinterpret_cast<const float *>(blob + kMlpB1)[i];
         B2[i] = reinterpret_cast<const float *>(blob + kMlpB2)[i];
@@ -187,7 +188,7 @@ __global__ void mlp_adam_kernel(float *__restrict__ master, unsigned char *__res
     master[i] = w;
     grad[i] = 0.0f;
     if (i < kPB1)
-        reinterpret_cast<uint16_t *>(blob)[i] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+        reinterpret_cast<uint16_t *>(blob)[mlp_blob_index(i)] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
     else
         reinterpret_cast<float *>(blob + kMlpB1)[i - kPB1] = w;
 }

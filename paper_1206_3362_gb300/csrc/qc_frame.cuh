@@ -93,7 +93,7 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
                     wv[i >> 2] |= (uint32_t)(*reinterpret_cast<const unsigned char *>(src + i)) << (8 * (i & 3));
             v = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
-        *reinterpret_cast<uint4 *>(stage + c * 16) = v;
+        *reinterpret_cast<uint4 *>(stage + c * 16) = clamp_m127(v);  // -128 decodes as -127
     }
     for (int i = t; i < NB * (int)H; i += G) SC[i] = 0x40004000u;
     group_sync<WPF>(bar_id);

@@ -244,6 +244,20 @@ def test_edge_frames(fwbf):
     assert (i < 0).any()
 
 
+@pytest.mark.parametrize("key,p", [("eg255", 16), ("rand504", 32), ("qc8192", 64)])
+def test_minus_128_reads_as_minus_127(fwbf, key, p):
+    """int8 inputs of -128 (outside the quantiser's range) decode as -127 in
+    every decoder (cyclic, list, quasi-cyclic), as the oracle reads them."""
+    h, c, y = frames(key, 24, 3.5, seed=14, zero=True)
+    q = oracle.quantize(y)
+    rng = np.random.default_rng(15)
+    q[rng.random(q.shape) < 0.05] = -128
+    q[0, :] = -128
+    i = assert_same(fwbf, h, p, q, 20, 1.5)
+    q127 = np.maximum(q, -127).astype(np.int8)
+    assert np.array_equal(i, assert_same(fwbf, h, p, q127, 20, 1.5))
+
+
 def test_frame_counts_ragged(fwbf):
     """n_frames 0, 1 and counts that leave warps, CTAs and the last 16-byte
     chunk of the buffer partly filled."""

@@ -84,7 +84,12 @@ def test_mlp_adam_step(fwbf):
     assert np.allclose(dm.cpu().numpy(), ref, atol=2e-6)
     assert not grad.any()
     w = blob[:9472].view(torch.int16).cpu().numpy().view(np.uint16).astype(np.uint32) << 16
-    assert np.array_equal(w.view(np.float32), mlp_ref.bf16_round(dm.cpu().numpy()[:4736]).astype(np.float32))
+    # the blob's order (include/fwbf.h): W1 and W3 as in the master vector, W2
+    # (unit u, input c) at group 64 (c // 8) + u, element c % 8
+    u, c = np.divmod(np.arange(4096), 64)
+    order = np.concatenate([np.arange(512), 512 + 512 * (c // 8) + 8 * u + c % 8, np.arange(4608, 4736)])
+    assert np.array_equal(w.view(np.float32)[order],
+                          mlp_ref.bf16_round(dm.cpu().numpy()[:4736]).astype(np.float32))
 
 
 # ---------------------------------------------------------------------------
@@ -151,46 +156,85 @@ def _varied_network():
     return net
 
 
+def _default_network(alpha):
+    """A network whose outputs are the fallback parameters for every input."""
+    from paper_1206_3362_gb300.learned import Network
+
+    net = Network(seed=9)
+    m = net.master.cpu().numpy()
+    m[4608:4736] = 0.0
+    m[4864:4866] = [alpha, 0.0]
+    net.set_master(m)
+    return net
+
+
 # eg1023 runs two warps per frame, eg4095 four
 @pytest.mark.parametrize("key,p,F,ebn0", [("eg1023", 8, 300, 3.25), ("eg4095", 64, 96, 3.75)])
 def test_decode_learned_replays_exactly(fwbf, key, p, F, ebn0):
     """The (alpha_q, theta_q) the network chose are recorded; the oracle run
-    with that schedule reproduces every frame solved in the learned passes, and
-    plain FWBF reproduces every frame handed to the fallback."""
+    with that schedule reproduces every frame the learned passes solved, and
+    every other frame carries plain FWBF's own result (the fallback).  The
+    learned body that records nothing gives the same results."""
     h, c, q = frames(key, F, ebn0, seed=44)
     k_learn, K = 6, 60
     net = _varied_network()
     with fwbf.Code.from_parity_check(h, p) as code:
         bits, iters = code.outputs(F)
         sched = torch.full((F, k_learn, 2), -1, dtype=torch.int32, device="cuda")
-        fwbf.fwbf_decode_learned(code.handle, torch.from_numpy(q).cuda(), K, k_learn, 1.5, net.blob, bits, iters,
-                                 out_sched=sched)
+        qd = torch.from_numpy(q).cuda()
+        fwbf.fwbf_decode_learned(code.handle, qd, K, k_learn, 1.5, net.blob, bits, iters, out_sched=sched)
+        b2, i2 = code.outputs(F)
+        fwbf.fwbf_decode_learned(code.handle, qd, K, k_learn, 1.5, net.blob, b2, i2)
         torch.cuda.synchronize()
+    assert torch.equal(iters, i2) and torch.equal(bits, b2)
     it = iters.cpu().numpy()
     b = bits.cpu().numpy().view(np.uint32)
     s = sched.cpu().numpy()
-    assert len(np.unique(s[:, 0, 0])) > 3  # the network really varies alpha
-    learned = (it >= 0) & (it <= k_learn)
+    used = s[s[:, :, 0] >= 0]  # (alpha_q, theta_q) of every learned pass that ran
+    # the network really varies both parameters, and some passes keep plain FWBF's
+    assert len(np.unique(used[:, 0])) >= 3 and len(np.unique(used[:, 1])) >= 2
+    assert ((used[:, 0] == 384) & (used[:, 1] == 0)).any()
     A = np.full((F, K), 384, dtype=np.int32)
     T = np.zeros((F, K), dtype=np.int32)
     A[:, :k_learn] = np.where(s[:, :, 0] >= 0, s[:, :, 0], 384)
     T[:, :k_learn] = np.where(s[:, :, 1] >= 0, s[:, :, 1], 0)
-    bo, io = oracle.fwbf_i8(h, p, q[learned], K, alpha_sched=A[learned], theta_sched=T[learned])
-    assert np.array_equal(io, it[learned]) and np.array_equal(bo, b[learned])
+    bo, io = oracle.fwbf_i8(h, p, q, K, alpha_sched=A, theta_sched=T)
+    learned = (io >= 0) & (io <= k_learn)  # solved within the learned passes
+    assert learned.sum() >= 8 and (~learned).sum() >= 8
+    assert np.array_equal(io[learned], it[learned]) and np.array_equal(bo[learned], b[learned])
     fb = ~learned
     bp, ip = oracle.fwbf_i8(h, p, q[fb], K, alpha=1.5)
-    assert np.array_equal(bp, b[fb])
-    assert np.array_equal(np.where(ip >= 0, ip + k_learn, ip), it[fb])
+    assert np.array_equal(bp, b[fb]) and np.array_equal(ip, it[fb])
+
+
+@pytest.mark.parametrize("key,p,F,ebn0", [("eg1023", 8, 400, 3.0), ("eg4095", 64, 96, 3.75)])
+def test_learned_default_network_is_plain(fwbf, key, p, F, ebn0):
+    """A network that always answers the fallback parameters (alpha 1.5,
+    threshold 0) decodes every frame exactly as plain FWBF does: no pass
+    deviates, so frames still unsolved after k_learn passes continue from
+    plain FWBF's own state, and a gated pass without flips is plain FWBF's
+    fixed point."""
+    h, c, q = frames(key, F, ebn0, seed=46)
+    net = _default_network(1.5)
+    with fwbf.Code.from_parity_check(h, p) as code:
+        bits, iters = code.outputs(F)
+        fwbf.fwbf_decode_learned(code.handle, torch.from_numpy(q).cuda(), 60, 3, 1.5, net.blob, bits, iters)
+        torch.cuda.synchronize()
+    it = iters.cpu().numpy()
+    bp, ip = oracle.fwbf_i8(h, p, q, 60, alpha=1.5)
+    assert (it > 3).sum() > 0 and (it < 0).sum() > 0  # continued frames and failures are both covered
+    assert np.array_equal(ip, it) and np.array_equal(bp, bits.cpu().numpy().view(np.uint32))
 
 
 @pytest.mark.parametrize("key,p,F,ebn0", [("eg1023", 8, 120, 3.25), ("eg4095", 64, 48, 3.75)])
 def test_learned_schedule_is_network_output(fwbf, key, p, F, ebn0):
     """Every (alpha_q, theta_q) a learned pass used is the network of the
-    float64 oracle evaluated on that pass's recorded features: alpha_q =
-    rne(256 clamp(o0, 0, 64)), theta_q = rne(256 clamp(16 o1, 0, 4096)).  The
-    kernel computes in float32 (an error below 1e-5 per output for these
-    weights), so each integer lies within half a unit of the exact value plus
-    256 x 1e-5 (alpha_q) or 4096 x 1e-5 (theta_q)."""
+    float64 oracle evaluated on that pass's recorded features, snapped to the
+    grid: alpha_q = 128 rne(2 clamp(o0, 0, 64)), theta_q = 1024 rne(clamp(4 o1,
+    0, 1024)).  The kernel computes in float32 (an error below 1e-5 per output
+    for these weights), so where the exact value lies within 1e-4 of a
+    rounding boundary either neighbour is accepted.  Passes with a syndrome
+    weight below 6 d_v use the fallback parameters (alpha_q 384, theta_q 0)."""
     h, c, q = frames(key, F, ebn0, seed=45)
     k_learn, K = 6, 60
     net = _varied_network()
@@ -203,14 +247,27 @@ def test_learned_schedule_is_network_output(fwbf, key, p, F, ebn0):
         torch.cuda.synchronize()
     s = sched.cpu().numpy().reshape(-1, 2)
     x = feat.cpu().numpy().reshape(-1, 8)
-    ran = s[:, 0] >= 0
+    dv = int(np.max(h.col_weights()))
+    W = np.rint(x[:, 0].astype(np.float64) * h.N)
+    gated = (s[:, 0] >= 0) & (W < 6 * dv)
+    assert gated.any()
+    assert (s[gated, 0] == 384).all() and (s[gated, 1] == 0).all()
+    ran = (s[:, 0] >= 0) & ~gated
     assert ran.sum() > F and not np.isnan(x[ran]).any()
     out, _ = mlp_ref.forward(net.master.cpu().numpy(), x[ran].astype(np.float64))
-    aq = 256.0 * np.clip(out[:, 0], 0.0, 64.0)
-    tq = 256.0 * np.clip(16.0 * out[:, 1], 0.0, 4096.0)
-    assert np.abs(s[ran, 0] - aq).max() <= 0.5 + 256 * 1e-5
-    assert np.abs(s[ran, 1] - tq).max() <= 0.5 + 4096 * 1e-5
-    assert len(np.unique(s[ran, 0])) > 3 and len(np.unique(s[ran, 1])) > 3
+
+    def snapped_ok(got, v, unit):
+        # got / unit must be rne(v), or either neighbour of a near-tie
+        lo, hi = np.floor(v), np.ceil(v)
+        near_tie = np.abs(v - np.floor(v) - 0.5) < 1e-4
+        want = np.round(v)  # round half to even, as the kernel's rne
+        k = got / unit
+        return (k == want) | (near_tie & ((k == lo) | (k == hi)))
+
+    assert (s[ran] % [128, 1024] == 0).all()
+    assert snapped_ok(s[ran, 0], 2.0 * np.clip(out[:, 0], 0.0, 64.0), 128).all()
+    assert snapped_ok(s[ran, 1], np.clip(4.0 * out[:, 1], 0.0, 1024.0), 1024).all()
+    assert len(np.unique(s[ran, 0])) >= 3 and len(np.unique(s[ran, 1])) >= 2
 
 
 def test_batched_learned_job_equals_single_code(fwbf):
@@ -254,9 +311,42 @@ def test_batched_learned_job_equals_single_code(fwbf):
 
 
 def test_trained_network_gain(fwbf):
-    """Train on frames plain FWBF labels itself, then compare on held-out
-    frames: the learned schedule (with plain fallback) must not lose frames
-    plain FWBF decodes, and must keep at most the plain frame error count."""
+    """What the committed EG(1023,781) network gains over the method without
+    it, on 2^18 held-out seeded frames at 4 dB: plain FWBF with the same block
+    length and weighting factor (the learned decoder's own fallback) against
+    the learned schedule.  The learned frame error rate's 95 % Wilson interval
+    lies entirely below plain FWBF's, and no frame that plain FWBF decodes to
+    the transmitted codeword is lost."""
+    from paper_1206_3362_gb300 import learned
+    from paper_1206_3362_gb300.inputs import Encoder
+
+    h = make_code("eg1023")
+    enc = Encoder(h)
+    net = learned.Network()
+    meta = net.load(learned.DEFAULT_WEIGHTS)
+    p, alpha, k_learn = int(meta["seg_len"]), float(meta["alpha_default"]), int(meta["k_learn"])
+    with fwbf.Code.from_parity_check(h, p) as code:
+        q, c = learned.make_frames(code, enc, 1 << 18, (4.0,), seed=4242, device="cuda")
+        bp, ip = code.outputs(q.shape[0])
+        fwbf.fwbf_decode(code.handle, q, 100, alpha, bp, ip)
+        bl, il = code.outputs(q.shape[0])
+        fwbf.fwbf_decode_learned(code.handle, q, 100, k_learn, alpha, net.blob, bl, il)
+        torch.cuda.synchronize()
+    ok_plain = learned.frame_ok(bp, ip, c)
+    ok_learned = learned.frame_ok(bl, il, c)
+    n = q.shape[0]
+    fe_plain, fe_learned = int((~ok_plain).sum()), int((~ok_learned).sum())
+    lo_plain, _ = learned.wilson(fe_plain, n)
+    _, hi_learned = learned.wilson(fe_learned, n)
+    print(f"frame errors: plain {fe_plain}, learned {fe_learned} of {n}")
+    assert hi_learned < lo_plain
+    assert int((ok_plain & ~ok_learned).sum()) == 0
+
+
+def test_train_pipeline_smoke(fwbf):
+    """Labels, features and training from scratch on 2^15 frames (a quick run
+    of the whole pipeline): the loss falls, and on held-out frames the new
+    network keeps at most the plain frame error count plus a small margin."""
     from paper_1206_3362_gb300 import learned
     from paper_1206_3362_gb300.inputs import Encoder
 
@@ -271,4 +361,4 @@ def test_trained_network_gain(fwbf):
         plain = learned.evaluate(code, q, c, None, sch, reps=1)
         lrn = learned.evaluate(code, q, c, net, sch, reps=1)
     print("plain", plain, "learned", lrn, "train", summary)
-    assert lrn["frame_errors"] <= plain["frame_errors"] + 3
+    assert lrn["frame_errors"] <= plain["frame_errors"] * 1.1 + 5
