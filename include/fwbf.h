@@ -217,6 +217,8 @@ typedef struct {
     const void *mlp;       /* NULL: plain FWBF; else the learned network (see
                               fwbf_decode_learned), cyclic codes with packed = 1 or 2 */
     int32_t k_learn;       /* learned passes before the plain fallback (mlp != NULL) */
+    int32_t gate_dv;       /* network consulted on learned passes with W_k >= gate_dv d_v
+                              (see fwbf_decode_learned) */
 } fwbf_batch_job;
 
 /*
@@ -302,9 +304,12 @@ int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t ma
  * network on the features above: outputs (o0, o1) give alpha = o0 and
  * theta = 16 o1 (in units of the int8 metric; theta_q = 256 theta),
  * then snapped to steps of 1/2 (alpha) and 4 (theta) and clamped to [0, 64]
- * and [0, 4096].  A pass whose syndrome weight W_k is below 6 d_v (six times
- * the largest column weight: about six bit errors' worth of unsatisfied
- * checks) does not evaluate the network and uses (alpha_fallback, 0).
+ * and [0, 4096].  The network is consulted only on passes whose syndrome
+ * weight W_k is at least gate_dv d_v (d_v the largest column weight: about
+ * gate_dv bit errors' worth of unsatisfied checks, the passes whose labels
+ * most often differ from plain FWBF's parameters); the other passes use
+ * (alpha_fallback, 0).  gate_dv >= 0 (0: every pass).  A larger gate evaluates
+ * the network less often (faster) and keeps less of its frame-error gain.
  * Fallback: a frame whose syndrome is not zero after k_learn learned passes
  * gets plain FWBF's own result for it (what fwbf_decode with alpha_fallback
  * and max_iter gives: decisions and pass count).  If every learned pass so far
@@ -325,7 +330,7 @@ int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t ma
  *   out_feat, feat_passes   as fwbf_decode_sched
  */
 int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter,
-                        int32_t k_learn, float alpha_fallback, const void *mlp,
+                        int32_t k_learn, int32_t gate_dv, float alpha_fallback, const void *mlp,
                         uint32_t *out_bits, int32_t *out_iters, int32_t *out_sched,
                         float *out_feat, int32_t feat_passes, void *stream);
 

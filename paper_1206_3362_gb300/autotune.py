@@ -13,6 +13,12 @@ Tuned per code, on seeded calibration frames at a chosen Eb/N0:
   batch, the number of warps per CTA and whether every frame is decoded by a
   group of warps ("lanes per frame": packed = 2).
 
+* the gate of the learned schedule (the network is consulted on passes with
+  W_k >= gate_dv d_v): a gate is admitted if it keeps at least half of the
+  network's frame-error gain, i.e. its frame errors are at most the midpoint
+  between those of the network consulted on every pass and those of plain
+  FWBF with the same p and alpha (select_gate).
+
 Among admitted settings the fastest (CUDA-event time of the decode) wins.
 Results are cached in a JSON file keyed by code, Eb/N0 and GPU name.
 """
@@ -107,6 +113,42 @@ def select_fastest_qualified(results, ref):
     qualified = [r for r in results
                  if r["frame_errors"] <= ref["frame_errors"] and r["bit_errors"] <= ref["bit_errors"]]
     return min(qualified, key=lambda r: r["ms"])
+
+
+GATE_CANDIDATES = (0, 6, 10, 12, 14, 16)
+
+
+def select_gate(results, plain):
+    """The fastest gate whose frame errors are at most the midpoint between
+    the ungated network's (gate_dv = 0, which must be measured) and plain
+    FWBF's; the ungated network always qualifies, ties in time keep the
+    earlier entry."""
+    full = next(r for r in results if r["gate_dv"] == 0)
+    limit = (full["frame_errors"] + plain["frame_errors"]) / 2.0
+    qualified = [r for r in results if r is full or r["frame_errors"] <= limit]
+    return min(qualified, key=lambda r: r["ms"])
+
+
+def tune_gate(code, q, c, net, alpha: float, k_learn: int, max_iter: int = 100, candidates=GATE_CANDIDATES,
+              reps: int = 3, log=None):
+    """Measures the learned decoder (network blob net.blob) at every gate
+    candidate and plain FWBF on the same calibration frames (q int8, c the
+    transmitted codewords) and picks the gate by select_gate."""
+    F = q.shape[0]
+    bits, iters = code.outputs(F)
+    ms = _time(lambda: fwbf.fwbf_decode(code.handle, q, max_iter, alpha, bits, iters), reps)
+    fe, be = _errors(bits, iters, c)
+    plain = {"frame_errors": fe, "bit_errors": be, "ms": ms}
+    results = []
+    for g in sorted(set(candidates) | {0}):
+        ms = _time(lambda: fwbf.fwbf_decode_learned(code.handle, q, max_iter, k_learn, alpha, net.blob, bits, iters,
+                                                    gate_dv=g), reps)
+        fe, be = _errors(bits, iters, c)
+        results.append({"gate_dv": g, "frame_errors": fe, "bit_errors": be, "ms": ms})
+        if log:
+            log(results[-1])
+    best = select_gate(results, plain)
+    return {"choice": best["gate_dv"], "plain": plain, "candidates": results, "frames": F}
 
 
 def tune_batch_shape(jobs, warps_candidates=(4, 8, 12, 16), packed_candidates=(2, 1, 0)):

@@ -48,7 +48,8 @@ struct CyclicParams {
     // 64-bit keys ((E' ^ 2^31) << 32 | (2^32 - 1 - n)); key_words uint32 words
     int ksh;
     uint32_t key_words;
-    int w_gate;           // learned passes with W below this use the fallback parameters
+    int gate_dv;          // learned passes with W < gate_dv d_v use the fallback parameters
+    int w_gate;           // gate_dv d_v (set by cyclic_layout)
 };
 
 __device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
@@ -180,16 +181,22 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         if (stats) {
             const int lo = off - 16 * c, hi = off + Z - 16 * c;  // frame bytes of the chunk: [lo, hi)
             const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+            const bool edge = lo > 0 || hi < 16;
+            uint32_t wc = 0u;  // per byte lane: values with |q| < 8 (at most 4)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int l = lo - 4 * i, h = hi - 4 * i;  // frame bytes of word i: [l, h)
-                uint32_t keep = l >= 4 || h <= 0 ? 0u : 0xffffffffu;
-                if (l > 0 && l < 4) keep <<= 8 * l;
-                if (h > 0 && h < 4) keep &= 0xffffffffu >> (8 * (4 - h));
+                uint32_t keep = 0xffffffffu;
+                if (edge) {
+                    const int l = lo - 4 * i, h = hi - 4 * i;  // frame bytes of word i: [l, h)
+                    keep = l >= 4 || h <= 0 ? 0u : keep;
+                    if (l > 0 && l < 4) keep <<= 8 * l;
+                    if (h > 0 && h < 4) keep &= 0xffffffffu >> (8 * (4 - h));
+                }
                 const uint32_t a = __vabsss4(wv[i]) & keep;  // |q| per byte (q >= -127)
                 sa += (int)__vsadu4(a, 0u);
-                sw += __popc(__vcmpltu4(a, 0x08080808u) & keep) >> 3;
+                wc += __vcmpltu4(a, 0x08080808u) & keep & 0x01010101u;
             }
+            sw += (int)__vsadu4(wc, 0u);
         }
     }
     if (stats) {
@@ -300,7 +307,6 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     group_sync<WPF>(bar_id);
 
     // ---- iterations ------------------------------------------------------
-    int Wprev = W, nflip_prev = 0, ncand_prev = 0;
     bool give_up = false;   // learned passes exhausted: fall back to plain FWBF
     bool deviated = false;  // a learned pass used parameters other than plain FWBF's
     for (int k = 0;; ++k) {
@@ -330,6 +336,21 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
             // features of this pass (feat[0..3], feat[4..7]), where something uses them
             float4 fa = make_float4(0.0f, 0.0f, 0.0f, 0.0f), fb = fa;
             if (!gated || (VAR == kVarAll && P.out_feat)) {
+                // the previous pass's (syndrome change, flips, candidates), summed
+                // over the group, are still in the group scratch its sum used
+                // (kept out of registers: the gather runs under a 64-register cap)
+                int Wprev = W, nflip_prev = 0, ncand_prev = 0;
+                if (k > 0) {
+                    const int *r = red + (WPF == 1 ? 0 : (rhalf ^ 1) * 4 * WPF);
+                    int dW = 0;
+#pragma unroll
+                    for (int w = 0; w < WPF; ++w) {
+                        dW += r[4 * w];
+                        nflip_prev += r[4 * w + 1];
+                        ncand_prev += r[4 * w + 2];
+                    }
+                    Wprev = W - dW;
+                }
                 const float4 st = *reinterpret_cast<const float4 *>(fstate);
                 fa = make_float4((float)W * P.inv_Z, (float)Wprev * P.inv_Z, st.z, (float)k * (1.0f / 16.0f));
                 fb = make_float4((float)nflip_prev * P.inv_B, (float)ncand_prev * P.inv_Z, st.x, st.y);
@@ -466,12 +487,16 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         }
         const int3 tot = group_sum3<WPF>(make_int3(warp_sum(dW), nflip, warp_sum(ncand)), red, rhalf, lane, gw,
                                          bar_id);
-        Wprev = W;
         W += tot.x;
         nflip = tot.y;
-        nflip_prev = nflip;
-        ncand_prev = tot.z;
-        if constexpr (WPF == 1) __syncwarp();
+        if constexpr (WPF == 1) {  // (one warp: the sums are kept where a group's would be)
+            if (VAR != kVarPlain && lane == 0) {
+                red[0] = tot.x;
+                red[1] = tot.y;
+                red[2] = tot.z;
+            }
+            __syncwarp();
+        }
         if (nflip == 0 && mode == kModePlain) {  // fixed point: every later pass repeats this one
             iters = -P.max_iter;
             break;
@@ -547,10 +572,7 @@ inline void cyclic_layout(const fwbf_code_s *c, CyclicParams &P) {
         const uint64_t emax = 256ull * 127ull * (uint64_t)c->dv_max;  // largest positive E'
         P.ksh = (emax << sh) < (1ull << 32) ? sh : -1;
         P.key_words = (uint32_t)c->B * (P.ksh >= 0 ? 1u : 2u);
-        // learned passes with fewer unsatisfied checks than about six bit errors
-        // make use the fallback parameters (98 % of such passes are labelled
-        // with them on EG(1023,781) at 3.0-4.5 dB)
-        P.w_gate = 6 * c->dv_max;
+        P.w_gate = P.gate_dv * c->dv_max;
     }
     o += a16(4 * P.key_words);
     P.off_red = o;  // group sums: 2 halves x 4 ints per warp of the group; then 4 floats for the network

@@ -286,8 +286,9 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
         if (reinterpret_cast<uintptr_t>(in.y) % 16) return fail(FWBF_EINVAL, "job y must be 16-byte aligned");
         if (in.mlp && (!packed || !cyclic_eligible(c)))
             return fail(FWBF_EUNSUPPORTED, "a learned job needs a cyclic code and the packed decoder");
-        if (in.mlp && (in.k_learn < 1 || reinterpret_cast<uintptr_t>(in.mlp) % 16))
-            return fail(FWBF_EINVAL, "learned job: k_learn < 1 or unaligned network blob");
+        if (in.mlp && (in.k_learn < 1 || in.gate_dv < 0 || in.gate_dv > 65535 ||
+                       reinterpret_cast<uintptr_t>(in.mlp) % 16))
+            return fail(FWBF_EINVAL, "learned job: k_learn < 1, gate_dv outside [0, 65535] or unaligned network blob");
         BatchJob &b = hj[j];
         b = BatchJob{};
         const int aq = (int)nearbyint((double)in.alpha * 256.0);
@@ -304,6 +305,7 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
                 b.cp.mode = kModeLearned;
                 b.cp.mlp = static_cast<const unsigned char *>(in.mlp);
                 b.cp.k_learn = in.k_learn;
+                b.cp.gate_dv = in.gate_dv;
             }
             cyclic_layout(c, b.cp);
             const int R = cyclic_R(c);

@@ -116,6 +116,7 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
         P.sched_stride = modes->sched_stride;
         P.mlp = modes->mlp;
         P.k_learn = modes->k_learn;
+        P.gate_dv = modes->gate_dv;
         P.out_sched = modes->out_sched;
         P.out_feat = modes->out_feat;
         P.feat_passes = modes->feat_passes;

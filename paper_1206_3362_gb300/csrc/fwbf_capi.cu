@@ -311,12 +311,13 @@ int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t ma
 }
 
 int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, int32_t k_learn,
-                        float alpha_fallback, const void *mlp, uint32_t *out_bits, int32_t *out_iters,
+                        int32_t gate_dv, float alpha_fallback, const void *mlp, uint32_t *out_bits, int32_t *out_iters,
                         int32_t *out_sched, float *out_feat, int32_t feat_passes, void *stream) {
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha_fallback, out_bits, out_iters);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
     if (k_learn < 1) return fail(FWBF_EINVAL, "k_learn must be >= 1");
+    if (gate_dv < 0 || gate_dv > 65535) return fail(FWBF_EINVAL, "gate_dv must be in [0, 65535]");
     if (!mlp || reinterpret_cast<uintptr_t>(mlp) % 16) return fail(FWBF_EINVAL, "mlp blob NULL or unaligned");
     if (out_feat && feat_passes < 1) return fail(FWBF_EINVAL, "feat_passes < 1");
     if (n_frames == 0) return FWBF_OK;
@@ -324,6 +325,7 @@ int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
     m.mode = 2;
     m.mlp = static_cast<const unsigned char *>(mlp);
     m.k_learn = k_learn;
+    m.gate_dv = gate_dv;
     m.out_sched = out_sched;
     m.out_feat = out_feat;
     m.feat_passes = out_feat ? feat_passes : 0;

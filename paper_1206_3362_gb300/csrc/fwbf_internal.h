@@ -62,6 +62,7 @@ struct CyclicModes {
     long long sched_stride = 0;
     const unsigned char *mlp = nullptr;
     int k_learn = 0;
+    int gate_dv = 0;
     int32_t *out_sched = nullptr;
     float *out_feat = nullptr;
     int feat_passes = 0;

@@ -171,7 +171,7 @@ def _errors(bits, iters, pool_c, chunk=1 << 15):
     return fe, be
 
 
-def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, max_iter: int = 100):
+def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, max_iter: int = 100, clocks=None):
     import time
 
     import torch
@@ -194,7 +194,7 @@ def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, ma
         _, pool_c = random_codewords_torch(enc, pool, seed=4000 + ci, device=dev)
         tune = autotune.tune_code(h, enc, SCALE4_EBN0[1], p_ref=p_ref, alpha_ref=1.5, frames=1 << 14)
         p_t, a_t = tune["choice"]["p"], tune["choice"]["alpha"]
-        net, k_learn = None, 0
+        net, k_learn, gate = None, 0, None
         wpath = (weights or {}).get(key, weights_path(key))
         if os.path.exists(wpath):
             net = Network(alpha_default=a_t)
@@ -203,13 +203,20 @@ def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, ma
         code_ref = fwbf.Code.from_parity_check(h, p_ref)
         code_t = fwbf.Code.from_parity_check(h, p_t)
         handles += [code_ref, code_t]
+        if net is not None:  # the gate of the learned schedule, on calibration frames at the lowest point
+            qcal = _pool_frames(enc, pool_c, 1 << 16, SCALE4_EBN0[0], seed=6000 + ci, device=dev)
+            ccal = pool_c[torch.arange(1 << 16, device=dev) % pool_c.shape[0]]
+            gate = autotune.tune_gate(code_t, qcal, ccal, net, a_t, k_learn, max_iter=max_iter, reps=2)
+            del qcal, ccal
         out["codes"][key] = {"N": h.N, "K": enc.K, "rate": enc.rate, "p_paper": p_ref, "p_tuned": p_t,
                              "alpha_tuned": a_t, "learned": net is not None, "k_learn": k_learn,
+                             "gate_dv": gate["choice"] if gate else None, "gate_tuning": gate,
                              "codeword_pool": pool, "autotune": tune["choice"]}
         for pi, eb in enumerate(SCALE4_EBN0):
             q = _pool_frames(enc, pool_c, per_job, eb, seed=5000 + 10 * ci + pi, device=dev)
             jobs.append(dict(key=key, ebn0=eb, K=enc.K, q=q, pool_c=pool_c, code_ref=code_ref, code_t=code_t,
-                             a_t=a_t, net=net, k_learn=k_learn, plain=code_ref.outputs(per_job, dev),
+                             a_t=a_t, net=net, k_learn=k_learn, gate_dv=gate["choice"] if gate else 0,
+                             plain=code_ref.outputs(per_job, dev),
                              batched=code_t.outputs(per_job, dev)))
     torch.cuda.synchronize()
     out["generate_seconds"] = time.time() - t0
@@ -223,11 +230,15 @@ def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, ma
     plain()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.mark("plain")
     e0.record()
     for _ in range(reps):
         plain()
     e1.record()
     torch.cuda.synchronize()
+    if clocks:
+        clocks.unmark("plain")
     ms_plain = e0.elapsed_time(e1) / reps
 
     # learned + batched: one graph-captured launch over every code and point
@@ -235,7 +246,7 @@ def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, ma
     for j in jobs:
         job = (j["code_t"].handle, j["q"], max_iter, j["a_t"], *j["batched"])
         if j["net"] is not None:
-            job = job + (j["net"].blob, j["k_learn"])
+            job = job + (j["net"].blob, j["k_learn"], j["gate_dv"])
         spec.append(job)
     # CTA shape tuned on 1/16 of every job's frames (the packed decoder with and
     # without warp groups; the list decoder gives the same results, slower)
@@ -255,11 +266,15 @@ def scale4(frames: int = 1 << 22, reps: int = 2, weights: dict | None = None, ma
             g.replay()
             torch.cuda.synchronize()
             b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if clocks:
+                clocks.mark("learned_batched")
             b0.record(s)
             for _ in range(reps):
                 g.replay()
             b1.record(s)
         torch.cuda.synchronize()
+        if clocks:
+            clocks.unmark("learned_batched")
         assert fwbf.fwbf_batch_status() == 0
         ms_batched = b0.elapsed_time(b1) / reps
     finally:

@@ -38,7 +38,8 @@ class FwbfError(RuntimeError):
 class BatchJob(ctypes.Structure):
     _fields_ = [("code", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
                 ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("out_bits", ctypes.c_void_p),
-                ("out_iters", ctypes.c_void_p), ("mlp", ctypes.c_void_p), ("k_learn", ctypes.c_int32)]
+                ("out_iters", ctypes.c_void_p), ("mlp", ctypes.c_void_p), ("k_learn", ctypes.c_int32),
+                ("gate_dv", ctypes.c_int32)]
 
 
 class CodeInfo(ctypes.Structure):
@@ -74,7 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_probe_bounded_wait": ([ctypes.c_uint32, P, P], ctypes.c_int),
         "fwbf_metric_f32": ([P, P, i64, f32, P, P], ctypes.c_int),
         "fwbf_decode_sched": ([P, P, i64, i32, P, P, i64, P, P, P, i32, P], ctypes.c_int),
-        "fwbf_decode_learned": ([P, P, i64, i32, i32, f32, P, P, P, P, P, i32, P], ctypes.c_int),
+        "fwbf_decode_learned": ([P, P, i64, i32, i32, i32, f32, P, P, P, P, P, i32, P], ctypes.c_int),
         "fwbf_mlp_pack": ([P, P, P], ctypes.c_int),
         "fwbf_mlp_forward": ([P, P, i64, P, P], ctypes.c_int),
         "fwbf_mlp_grad": ([P, P, P, i64, i64, P, P, P], ctypes.c_int),
@@ -316,9 +317,10 @@ def fwbf_decode_sched(code, y, max_iter: int, alpha_q, theta_q, out_bits, out_it
 
 
 def fwbf_decode_learned(code, y, max_iter: int, k_learn: int, alpha_fallback: float, mlp_blob, out_bits,
-                        out_iters, out_sched=None, out_feat=None, stream=None) -> None:
+                        out_iters, out_sched=None, out_feat=None, stream=None, gate_dv: int = 6) -> None:
     """Learned per-pass schedule (network blob: uint8 CUDA tensor of
-    MLP_BLOB_BYTES), plain FWBF fallback after k_learn passes."""
+    MLP_BLOB_BYTES), consulted on passes with W_k >= gate_dv d_v, plain FWBF
+    fallback after k_learn passes."""
     import torch
 
     info = fwbf_code_query(code)
@@ -328,7 +330,7 @@ def fwbf_decode_learned(code, y, max_iter: int, k_learn: int, alpha_fallback: fl
     _need(out_sched, F * int(k_learn) * 2, "out_sched")
     fp = _feat(F, out_feat)
     _check(load_library().fwbf_decode_learned(code, _dev(y, torch.int8, "y"), F, int(max_iter), int(k_learn),
-                                              float(alpha_fallback), _dev(mlp_blob, torch.uint8, "mlp_blob"),
+                                              int(gate_dv), float(alpha_fallback), _dev(mlp_blob, torch.uint8, "mlp_blob"),
                                               _dev(out_bits, torch.int32, "out_bits"),
                                               _dev(out_iters, torch.int32, "out_iters"),
                                               _opt(out_sched, torch.int32, "out_sched"),
@@ -385,7 +387,7 @@ def fwbf_mlp_adam(master, blob, grad, m, v, step: int, lr: float, beta1=0.9, bet
 
 def fwbf_batch_create(jobs, warps_per_cta: int = 16, packed: int = 1) -> ctypes.c_void_p:
     """jobs: list of (code handle, y int8 [F][N], max_iter, alpha, out_bits,
-    out_iters[, mlp blob uint8 tensor, k_learn])."""
+    out_iters[, mlp blob uint8 tensor, k_learn[, gate_dv (default 6)]])."""
     import torch
 
     arr = (BatchJob * len(jobs))()
@@ -394,6 +396,7 @@ def fwbf_batch_create(jobs, warps_per_cta: int = 16, packed: int = 1) -> ctypes.
         if len(job) > 6 and job[6] is not None:
             arr[i].mlp = _dev(job[6], torch.uint8, "mlp").value
             arr[i].k_learn = int(job[7])
+            arr[i].gate_dv = int(job[8]) if len(job) > 8 else 6
         arr[i].code = code.value if isinstance(code, ctypes.c_void_p) else code
         N = fwbf_code_query(code).N
         F = _frames(y, N)

@@ -42,6 +42,7 @@ class Schedule:
     grid_alpha: tuple = (1.0, 1.5, 2.0, 2.5, 3.0)
     grid_theta: tuple = (0.0, 4.0, 8.0)   # in units of the int8 metric
     k_learn: int = 8
+    gate_dv: int = 6          # the network is consulted on passes with W_k >= gate_dv d_v
     label_max_iter: int = 30
 
 
@@ -225,7 +226,7 @@ def evaluate(code, q, c, net: Network | None, sch: Schedule, max_iter: int = 100
             fwbf.fwbf_decode(code.handle, q, max_iter, sch.alpha_default, bits, iters)
         else:
             fwbf.fwbf_decode_learned(code.handle, q, max_iter, sch.k_learn, sch.alpha_default, net.blob, bits,
-                                     iters)
+                                     iters, gate_dv=sch.gate_dv)
 
     run()
     torch.cuda.synchronize()
@@ -300,7 +301,7 @@ def evaluate_batched(code, q, c, net: Network | None, sch: Schedule, max_iter: i
     bits, iters = code.outputs(F, q.device)
     job = (code.handle, q, max_iter, sch.alpha_default, bits, iters)
     if net is not None:
-        job = job + (net.blob, sch.k_learn)
+        job = job + (net.blob, sch.k_learn, sch.gate_dv)
     batch = fwbf.fwbf_batch_create([job], warps_per_cta=warps_per_cta, packed=2)
     s = torch.cuda.Stream()
     try:

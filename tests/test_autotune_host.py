@@ -58,3 +58,21 @@ def test_cache_ignores_a_damaged_file(tmp_path):
     with open(path, "w") as f:
         f.write("{not json")
     assert autotune.Cache(path).get("k") is None
+
+
+def _g(gate, fe, ms):
+    return {"gate_dv": gate, "frame_errors": fe, "bit_errors": 10 * fe, "ms": ms}
+
+
+def test_gate_keeps_half_the_network_gain():
+    """Ungated network 100 frame errors, plain FWBF 300: gates with at most
+    200 qualify; the fastest of them wins, a faster gate with 201 does not."""
+    plain = {"frame_errors": 300, "bit_errors": 3000, "ms": 10.0}
+    results = [_g(0, 100, 12.0), _g(6, 110, 11.5), _g(12, 200, 10.8), _g(16, 201, 10.1)]
+    assert autotune.select_gate(results, plain) is results[2]
+
+
+def test_ungated_network_always_qualifies():
+    plain = {"frame_errors": 90, "bit_errors": 900, "ms": 10.0}
+    results = [_g(0, 100, 12.0), _g(6, 96, 11.0), _g(12, 96, 10.5)]
+    assert autotune.select_gate(results, plain) is results[0]

@@ -22,7 +22,8 @@ class _Recorder:
         def call(*args):
             if name == "fwbf_batch_create":  # copy the job table while the caller still owns it
                 jobs = ctypes.cast(args[0], ctypes.POINTER(fwbf.BatchJob))
-                self.jobs = [(jobs[i].n_frames, jobs[i].max_iter, jobs[i].k_learn) for i in range(args[1])]
+                self.jobs = [(jobs[i].n_frames, jobs[i].max_iter, jobs[i].k_learn, jobs[i].gate_dv)
+                             for i in range(args[1])]
             self.calls.append((name, args))
             return 0
         return call
@@ -87,7 +88,10 @@ def test_schedules_and_learned(lib):
     blob = torch.zeros(fwbf.MLP_BLOB_BYTES, dtype=torch.uint8)
     sched = torch.zeros((F, 3, 2), dtype=torch.int32)
     fwbf.fwbf_decode_learned(1, y, K, 3, 1.5, blob, bits, iters, out_sched=sched, out_feat=feat)
-    assert lib.calls[-1][0] == "fwbf_decode_learned" and lib.calls[-1][1][11] == 4
+    name, args = lib.calls[-1]
+    assert name == "fwbf_decode_learned" and args[4:7] == (3, 6, 1.5) and args[12] == 4  # k_learn, gate, alpha
+    fwbf.fwbf_decode_learned(1, y, K, 3, 1.5, blob, bits, iters, gate_dv=0)
+    assert lib.calls[-1][1][5] == 0
     with pytest.raises(ValueError, match="out_sched"):
         fwbf.fwbf_decode_learned(1, y, K, 4, 1.5, blob, bits, iters, out_sched=sched)
     with pytest.raises(ValueError, match="mlp_blob"):
@@ -117,10 +121,11 @@ def test_batch_jobs(lib):
     y, bits, iters = _io(9)
     blob = torch.zeros(fwbf.MLP_BLOB_BYTES, dtype=torch.uint8)
     fwbf.fwbf_batch_create([(ctypes.c_void_p(1), y, 10, 1.5, bits, iters),
-                            (ctypes.c_void_p(2), y[:4], 20, 2.0, bits[:4], iters[:4], blob, 5)], 16, 2)
+                            (ctypes.c_void_p(2), y[:4], 20, 2.0, bits[:4], iters[:4], blob, 5),
+                            (ctypes.c_void_p(3), y[:2], 20, 2.0, bits[:2], iters[:2], blob, 4, 12)], 16, 2)
     name, args = lib.calls[-1]
-    assert name == "fwbf_batch_create" and args[1:4] == (2, 16, 2)
-    assert lib.jobs == [(9, 10, 0), (4, 20, 5)]
+    assert name == "fwbf_batch_create" and args[1:4] == (3, 16, 2)
+    assert lib.jobs == [(9, 10, 0, 0), (4, 20, 5, 6), (2, 20, 4, 12)]
     with pytest.raises(ValueError, match="out_bits"):
         fwbf.fwbf_batch_create([(ctypes.c_void_p(1), y, 10, 1.5, bits[:8], iters)])
     with pytest.raises(ValueError, match="mlp"):
