@@ -130,7 +130,9 @@ int fwbf_decode(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter
  * library holds until the process exits.  Arguments, results and errors are
  * those of fwbf_decode.
  *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture.
+ *     that first call before any stream capture.  The address is kept for the
+ *     life of the process: after cudaDeviceReset on that device it is stale,
+ *     so do not use this entry point on a device that has been reset.
  *   - The array is shared by every call and keeps the last call's contents; the
  *     counter is cleared on the stream before each launch.  Calls whose work
  *     overlaps on the GPU (other streams, other threads) race on it: order them
