@@ -255,6 +255,18 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
  */
 int fwbf_decode_batch(fwbf_batch b, void *stream);
 
+/* How a batch decodes job `job` (0 <= job < the batch's job count), as chosen
+ * at create time. */
+typedef struct {
+    int32_t decoder;          /* FWBF_DECODER_LIST, _CYCLIC or _QC */
+    int32_t warps_per_frame;  /* warps that decode one frame together */
+    int32_t frames_per_cta;   /* frames a CTA decodes at once for this job */
+    int32_t grouped;          /* 1: the launch is the grouped kernel (two 512-thread
+                                 CTAs per SM, every frame by a warp group) */
+} fwbf_batch_job_info;
+
+int fwbf_batch_query(fwbf_batch b, int32_t job, fwbf_batch_job_info *out);
+
 /* Waits for the stream; FWBF_ETIMEOUT if a batch kernel gave up a bounded wait. */
 int fwbf_batch_status(void *stream);
 

@@ -260,6 +260,7 @@ extern "C" {
 
 int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_per_cta, int32_t packed,
                       fwbf_batch *out) {
+    TraceRange trace("fwbf_batch_create");
     if (!out) return fail(FWBF_EINVAL, "out is NULL");
     *out = nullptr;
     if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs) return fail(FWBF_EINVAL, "n_jobs must be in [1, 16]");
@@ -478,6 +479,7 @@ int fwbf_batch_create(const fwbf_batch_job *jobs, int32_t n_jobs, int32_t warps_
 }
 
 int fwbf_decode_batch(fwbf_batch b, void *stream) {
+    TraceRange trace("fwbf_decode_batch");
     if (!b) return fail(FWBF_EINVAL, "batch is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * b->n_jobs, s);
@@ -490,6 +492,18 @@ int fwbf_decode_batch(fwbf_batch b, void *stream) {
         fwbf_decode_batch_kernel<false, false><<<b->blocks, b->threads, b->dyn, s>>>(b->params);
     e = cudaGetLastError();
     return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "decode_batch launch");
+}
+
+int fwbf_batch_query(fwbf_batch b, int32_t job, fwbf_batch_job_info *out) {
+    if (!b || !out) return fail(FWBF_EINVAL, "batch or out is NULL");
+    if (job < 0 || job >= b->n_jobs) return fail(FWBF_EINVAL, "job index out of range");
+    const BatchJob &J = b->params.jobs[job];
+    out->decoder = job_is_qc(J.kind) ? FWBF_DECODER_QC : job_is_cyclic(J.kind) ? FWBF_DECODER_CYCLIC
+                                                                             : FWBF_DECODER_LIST;
+    out->warps_per_frame = J.wpf;
+    out->frames_per_cta = J.wpf > 0 ? J.warps / J.wpf : 0;
+    out->grouped = b->grouped ? 1 : 0;
+    return FWBF_OK;
 }
 
 int fwbf_batch_destroy(fwbf_batch b) {

@@ -296,21 +296,15 @@ int launch_decode_f32(const fwbf_code_s *c, const float *y, int64_t n_frames, in
     const int64_t need = (n_frames + warps - 1) / warps;
     if (blocks > need) blocks = need;
 
-    unsigned long long *counter = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(counter, s);
-        return cuda_fail(e, "cudaMemsetAsync");
-    }
-    P.counter = counter;
+    CounterLease ctr;
+    int rc = acquire_counter(c, s, &ctr);
+    if (rc) return rc;
+    P.counter = ctr.ptr;
     kern<<<(unsigned)blocks, warps * 32, dyn, s>>>(P);
     e = cudaGetLastError();
-    cudaError_t e2 = cudaFreeAsync(counter, s);
+    const int rc2 = release_counter(ctr, s);
     if (e != cudaSuccess) return cuda_fail(e, "decode_f32 launch");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync(frame counter)");
-    return 0;
+    return rc2;
 }
 
 }  // namespace fwbf

@@ -150,21 +150,22 @@ static int launch_i8_with_counter(const fwbf_code_s *c, const int8_t *y, int64_t
     return launch_generic_i8(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
 }
 
+int launch_decode_i8_with(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                          int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
+                          cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(frame counter)");
+    return launch_i8_with_counter(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
+}
+
 int launch_decode_i8(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
                      int theta_q, uint32_t *out_bits, int32_t *out_iters, cudaStream_t s) {
-    unsigned long long *counter = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(counter, s);
-        return cuda_fail(e, "cudaMemsetAsync");
-    }
-    const int rc = launch_i8_with_counter(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, counter, s);
-    e = cudaFreeAsync(counter, s);
+    CounterLease ctr;
+    int rc = acquire_counter(c, s, &ctr);
     if (rc) return rc;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(frame counter)");
-    return 0;
+    rc = launch_i8_with_counter(c, y, n_frames, max_iter, alpha_q, theta_q, out_bits, out_iters, ctr.ptr, s);
+    const int rc2 = release_counter(ctr, s);
+    return rc ? rc : rc2;
 }
 
 // ---------------------------------------------------------------------------
@@ -227,20 +228,12 @@ namespace fwbf {
 // lambda-largest selection: the list decoder with a per-frame candidate list
 int launch_decode_i8_lambda(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
                             int lambda, uint32_t *out_bits, int32_t *out_iters, cudaStream_t s) {
-    unsigned long long *counter = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(counter, s);
-        return cuda_fail(e, "cudaMemsetAsync");
-    }
-    const int rc =
-        launch_generic_i8(c, y, n_frames, max_iter, alpha_q, 0, out_bits, out_iters, counter, s, lambda);
-    e = cudaFreeAsync(counter, s);
+    CounterLease ctr;
+    int rc = acquire_counter(c, s, &ctr);
     if (rc) return rc;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(frame counter)");
-    return 0;
+    rc = launch_generic_i8(c, y, n_frames, max_iter, alpha_q, 0, out_bits, out_iters, ctr.ptr, s, lambda);
+    const int rc2 = release_counter(ctr, s);
+    return rc ? rc : rc2;
 }
 
 }  // namespace fwbf

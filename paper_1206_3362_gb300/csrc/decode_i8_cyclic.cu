@@ -171,25 +171,17 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
 
 namespace fwbf {
 
-// Scheduled and learned decoding: the cyclic kernel with a frame counter from
-// the stream-ordered allocator.
+// Scheduled and learned decoding: the cyclic kernel with the handle's frame
+// counter for the stream.
 int launch_decode_i8_modes(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
                            uint32_t *out_bits, int32_t *out_iters, const CyclicModes &modes, cudaStream_t s) {
     if (!cyclic_eligible(c)) return fail(FWBF_EUNSUPPORTED, "per-pass schedules need a cyclic code");
-    unsigned long long *counter = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&counter), sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(counter, s);
-        return cuda_fail(e, "cudaMemsetAsync");
-    }
-    const int rc = launch_decode_i8_cyclic(c, y, n_frames, max_iter, alpha_q, 0, out_bits, out_iters, counter, s,
-                                           &modes);
-    e = cudaFreeAsync(counter, s);
+    CounterLease ctr;
+    int rc = acquire_counter(c, s, &ctr);
     if (rc) return rc;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeAsync(frame counter)");
-    return 0;
+    rc = launch_decode_i8_cyclic(c, y, n_frames, max_iter, alpha_q, 0, out_bits, out_iters, ctr.ptr, s, &modes);
+    const int rc2 = release_counter(ctr, s);
+    return rc ? rc : rc2;
 }
 
 }  // namespace fwbf

@@ -69,6 +69,56 @@ static int detect_circulant(int N, int M, int64_t nnz, const int32_t *rows, cons
 
 using namespace fwbf;
 
+namespace fwbf {
+
+int acquire_counter(const fwbf_code_s *c, cudaStream_t s, CounterLease *out) {
+    *out = CounterLease{};
+    {
+        std::lock_guard<std::mutex> lock(c->counters.mu);
+        for (const auto &kv : c->counters.by_stream)
+            if (kv.first == s) out->ptr = kv.second;
+        if (!out->ptr) {
+            cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+                cudaGetLastError();
+                st = cudaStreamCaptureStatusActive;  // unknown: take the capturable path
+            }
+            if (st == cudaStreamCaptureStatusNone) {
+                unsigned long long *p = nullptr;
+                cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), sizeof(unsigned long long));
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(frame counter)");
+                c->counters.by_stream.emplace_back(s, p);
+                out->ptr = p;
+            }
+        }
+    }
+    if (!out->ptr) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&out->ptr), sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(frame counter)");
+        out->owned = true;
+    }
+    cudaError_t e = cudaMemsetAsync(out->ptr, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        release_counter(*out, s);
+        return cuda_fail(e, "cudaMemsetAsync(frame counter)");
+    }
+    return FWBF_OK;
+}
+
+int release_counter(const CounterLease &lease, cudaStream_t s) {
+    if (!lease.owned) return FWBF_OK;
+    cudaError_t e = cudaFreeAsync(lease.ptr, s);
+    return e == cudaSuccess ? FWBF_OK : cuda_fail(e, "cudaFreeAsync(frame counter)");
+}
+
+void free_counters(const fwbf_code_s *c) {
+    std::lock_guard<std::mutex> lock(c->counters.mu);
+    for (const auto &kv : c->counters.by_stream) cudaFree(kv.second);
+    c->counters.by_stream.clear();
+}
+
+}  // namespace fwbf
+
 extern "C" {
 
 const char *fwbf_strerror(int status) {
@@ -87,6 +137,7 @@ const char *fwbf_last_error(void) { return g_last_error.c_str(); }
 
 int fwbf_code_create(int32_t N, int32_t M, int64_t nnz, const int32_t *row_idx, const int32_t *col_idx,
                      int32_t seg_len, fwbf_code *out) {
+    TraceRange trace("fwbf_code_create");
     if (!out) return fail(FWBF_EINVAL, "out is NULL");
     *out = nullptr;
     if (N < 1 || N > 65535 || M < 1 || M > 65535)
@@ -224,6 +275,7 @@ int fwbf_code_create(int32_t N, int32_t M, int64_t nnz, const int32_t *row_idx, 
 int fwbf_destroy(fwbf_code c) {
     if (!c) return FWBF_OK;
     cudaError_t e = cudaDeviceSynchronize();
+    free_counters(c);
     cudaError_t e2 = cudaFree(c->d_table);
     delete c;
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
@@ -269,6 +321,7 @@ static int check_decode_args(fwbf_code c, const void *y, int64_t n_frames, int32
 
 int fwbf_decode(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, float alpha,
                 uint32_t *out_bits, int32_t *out_iters, void *stream) {
+    TraceRange trace("fwbf_decode");
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
@@ -280,6 +333,7 @@ int fwbf_decode(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter
 
 int fwbf_decode_noalloc(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, float alpha,
                         uint32_t *out_bits, int32_t *out_iters, void *stream) {
+    TraceRange trace("fwbf_decode_noalloc");
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
@@ -292,6 +346,7 @@ int fwbf_decode_noalloc(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
 int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, const int32_t *alpha_q,
                       const int32_t *theta_q, int64_t sched_stride, uint32_t *out_bits, int32_t *out_iters,
                       float *out_feat, int32_t feat_passes, void *stream) {
+    TraceRange trace("fwbf_decode_sched");
     int rc = check_decode_args(c, y, n_frames, max_iter, 1.0f, out_bits, out_iters);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
@@ -313,6 +368,7 @@ int fwbf_decode_sched(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t ma
 int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, int32_t k_learn,
                         int32_t gate_dv, float alpha_fallback, const void *mlp, uint32_t *out_bits, int32_t *out_iters,
                         int32_t *out_sched, float *out_feat, int32_t feat_passes, void *stream) {
+    TraceRange trace("fwbf_decode_learned");
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha_fallback, out_bits, out_iters);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
@@ -336,6 +392,7 @@ int fwbf_decode_learned(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t 
 
 int fwbf_decode_host(fwbf_code c, const float *y_host, int64_t n_frames, int32_t max_iter, float alpha,
                      uint32_t *bits_host, int32_t *iters_host, int64_t chunk_frames, void *stream) {
+    TraceRange trace("fwbf_decode_host");
     int rc = check_decode_args(c, y_host, n_frames, max_iter, alpha, bits_host, iters_host);
     if (rc) return rc;
     if (chunk_frames < 1) return fail(FWBF_EINVAL, "chunk_frames must be >= 1");
@@ -343,11 +400,13 @@ int fwbf_decode_host(fwbf_code c, const float *y_host, int64_t n_frames, int32_t
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
     const int64_t N = c->N, words = (N + 31) / 32;
     const int64_t chunk = chunk_frames < n_frames ? chunk_frames : n_frames;
-    // per buffer: float y | int8 q (16-byte aligned) | bits | iters
+    // per buffer: float y | int8 q (16-byte aligned) | bits | iters | frame counter
+    // (the pipeline's streams are its own, so are their counters)
     const size_t y_bytes = (size_t)(chunk * N) * 4, q_off = (y_bytes + 255) & ~(size_t)255;
     const size_t b_off = (q_off + (size_t)(chunk * N) + 255) & ~(size_t)255;
     const size_t i_off = (b_off + (size_t)(chunk * words) * 4 + 255) & ~(size_t)255;
-    const size_t buf_bytes = (i_off + (size_t)chunk * 4 + 255) & ~(size_t)255;
+    const size_t c_off = (i_off + (size_t)chunk * 4 + 255) & ~(size_t)255;
+    const size_t buf_bytes = c_off + 256;
     char *dev = nullptr;
     cudaStream_t st[2] = {nullptr, nullptr};
     cudaEvent_t ev_start = nullptr, ev_done[2] = {nullptr, nullptr};
@@ -370,11 +429,12 @@ int fwbf_decode_host(fwbf_code c, const float *y_host, int64_t n_frames, int32_t
         int8_t *qd = reinterpret_cast<int8_t *>(base + q_off);
         uint32_t *bd = reinterpret_cast<uint32_t *>(base + b_off);
         int32_t *id = reinterpret_cast<int32_t *>(base + i_off);
+        unsigned long long *cd = reinterpret_cast<unsigned long long *>(base + c_off);
         e = cudaMemcpyAsync(yd, y_host + f0 * N, (size_t)(nf * N) * 4, cudaMemcpyHostToDevice, st[b]);
         if (e != cudaSuccess) break;
         rc = launch_quantize(yd, qd, nf * N, st[b]);
         if (rc) break;
-        rc = launch_decode_i8(c, qd, nf, max_iter, (int)nearbyint((double)alpha * 256.0), 0, bd, id, st[b]);
+        rc = launch_decode_i8_with(c, qd, nf, max_iter, (int)nearbyint((double)alpha * 256.0), 0, bd, id, cd, st[b]);
         if (rc) break;
         e = cudaMemcpyAsync(bits_host + f0 * words, bd, (size_t)(nf * words) * 4, cudaMemcpyDeviceToHost, st[b]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(iters_host + f0, id, (size_t)nf * 4, cudaMemcpyDeviceToHost, st[b]);
@@ -398,6 +458,7 @@ int fwbf_decode_host(fwbf_code c, const float *y_host, int64_t n_frames, int32_t
 
 int fwbf_decode_lambda(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t max_iter, float alpha,
                        int32_t lambda, uint32_t *out_bits, int32_t *out_iters, void *stream) {
+    TraceRange trace("fwbf_decode_lambda");
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(y) % 16) return fail(FWBF_EINVAL, "y must be 16-byte aligned");
@@ -411,6 +472,7 @@ int fwbf_decode_lambda(fwbf_code c, const int8_t *y, int64_t n_frames, int32_t m
 
 int fwbf_decode_f32(fwbf_code c, const float *y, int64_t n_frames, int32_t max_iter, float alpha,
                     uint32_t *out_bits, int32_t *out_iters, void *stream) {
+    TraceRange trace("fwbf_decode_f32");
     int rc = check_decode_args(c, y, n_frames, max_iter, alpha, out_bits, out_iters);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(y) % 4) return fail(FWBF_EINVAL, "y must be 4-byte aligned");

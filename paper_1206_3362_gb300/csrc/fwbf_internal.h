@@ -3,11 +3,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "fwbf.h"
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
+
+// Frame work counters (8 bytes of device memory each) owned by a code handle,
+// one per stream the handle decodes on: calls on one stream are ordered, so
+// they share its counter; the handle frees them.
+struct StreamCounters {
+    std::mutex mu;
+    std::vector<std::pair<cudaStream_t, unsigned long long *>> by_stream;
+};
 
 // Index tables of H in circulant form (Z = 1: plain CSR/CSC).
 //   A check m = R*Z + i (block row R, offset i) has, for every entry (C, t) of
@@ -30,14 +42,38 @@ struct fwbf_code_s {
     int device;
     int num_sms;
     int smem_optin;             // max dynamic shared memory per block
+    mutable StreamCounters counters;
 };
 
 namespace fwbf {
+
+// An NVTX range over an entry point's host-side work (argument checks, set-up,
+// queueing), named after it, for timeline profilers; header-only NVTX costs a
+// few nanoseconds when no profiler is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // thread-local detail message for fwbf_last_error()
 void set_error(const std::string &msg);
 int fail(int status, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
+
+// A zeroed frame work counter for a decode on stream s: the handle's counter
+// for s, created by the first call on s; a first call made under stream
+// capture takes a stream-ordered allocation instead (owned = true), which
+// release_counter frees after the launch.
+struct CounterLease {
+    unsigned long long *ptr = nullptr;
+    bool owned = false;
+};
+int acquire_counter(const fwbf_code_s *c, cudaStream_t s, CounterLease *out);
+int release_counter(const CounterLease &lease, cudaStream_t s);
+// frees the handle's counters (after the device has finished with them)
+void free_counters(const fwbf_code_s *c);
 
 // status word of bounded waits: kernels OR a non-zero value into it
 int read_and_clear_status_i8(cudaStream_t s, int *out);
@@ -72,6 +108,10 @@ int launch_decode_i8_cyclic(const fwbf_code_s *c, const int8_t *y, int64_t n_fra
                             cudaStream_t s, const CyclicModes *modes = nullptr);
 int launch_decode_i8_modes(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
                            uint32_t *out_bits, int32_t *out_iters, const CyclicModes &modes, cudaStream_t s);
+// fwbf_decode's launch with a frame counter the caller provides (cleared here)
+int launch_decode_i8_with(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter, int alpha_q,
+                          int theta_q, uint32_t *out_bits, int32_t *out_iters, unsigned long long *counter,
+                          cudaStream_t s);
 int launch_decode_i8_noalloc(const fwbf_code_s *c, const int8_t *y, int64_t n_frames, int max_iter,
                              int alpha_q, int theta_q, uint32_t *out_bits, int32_t *out_iters,
                              cudaStream_t s);

@@ -35,6 +35,11 @@ class FwbfError(RuntimeError):
         self.status = status
 
 
+class BatchJobInfo(ctypes.Structure):
+    _fields_ = [("decoder", ctypes.c_int32), ("warps_per_frame", ctypes.c_int32),
+                ("frames_per_cta", ctypes.c_int32), ("grouped", ctypes.c_int32)]
+
+
 class BatchJob(ctypes.Structure):
     _fields_ = [("code", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n_frames", ctypes.c_int64),
                 ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("out_bits", ctypes.c_void_p),
@@ -81,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "fwbf_mlp_grad": ([P, P, P, i64, i64, P, P, P], ctypes.c_int),
         "fwbf_mlp_adam": ([P, P, P, P, P, i64, f32, f32, f32, f32, P], ctypes.c_int),
         "fwbf_batch_create": ([P, i32, i32, i32, ctypes.POINTER(P)], ctypes.c_int),
+        "fwbf_batch_query": ([P, i32, ctypes.POINTER(BatchJobInfo)], ctypes.c_int),
         "fwbf_decode_batch": ([P, P], ctypes.c_int),
         "fwbf_batch_status": ([P], ctypes.c_int),
         "fwbf_batch_destroy": ([P], ctypes.c_int),
@@ -417,6 +423,14 @@ def fwbf_batch_create(jobs, warps_per_cta: int = 16, packed: int = 1) -> ctypes.
 
 def fwbf_decode_batch(batch, stream=None) -> None:
     _check(load_library().fwbf_decode_batch(batch, _stream(stream)))
+
+
+def fwbf_batch_query(batch, job: int) -> BatchJobInfo:
+    """How the batch decodes job `job` (decoder, warps per frame, frames per
+    CTA, grouped kernel or not)."""
+    out = BatchJobInfo()
+    _check(load_library().fwbf_batch_query(batch, int(job), ctypes.byref(out)))
+    return out
 
 
 def fwbf_batch_status(stream=None) -> int:

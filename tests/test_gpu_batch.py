@@ -139,6 +139,13 @@ def test_batch_quasi_cyclic_jobs(fwbf, warps, packed):
         spec = [(j["code"].handle, j["qd"], 40, 1.5, b, it) for j, (b, it) in zip(jobs, outs)]
         batch = fwbf.fwbf_batch_create(spec, warps_per_cta=warps, packed=packed)
         try:
+            info = [fwbf.fwbf_batch_query(batch, k) for k in range(len(spec))]
+            # EG(255) (H / 32 = 4) keeps the grouped kernel out; the mixed kernel
+            # never gives a job 16 warps per frame (it would skip such a job)
+            assert not any(i.grouped for i in info)
+            assert all(i.warps_per_frame in (1, 2, 4, 8) for i in info)
+            assert [i.decoder for i in info] == [fwbf.FWBF_DECODER_QC, fwbf.FWBF_DECODER_QC, fwbf.FWBF_DECODER_LIST,
+                                                 fwbf.FWBF_DECODER_CYCLIC]
             fwbf.fwbf_decode_batch(batch)
             torch.cuda.synchronize()
             assert fwbf.fwbf_batch_status() == 0
@@ -153,6 +160,39 @@ def test_batch_quasi_cyclic_jobs(fwbf, warps, packed):
             bo, io = oracle.fwbf_i8(j["h"], j["p"], j["q"][idx], 40, alpha=1.5)
             assert np.array_equal(it.cpu().numpy()[idx], io), k
             assert np.array_equal(b.cpu().numpy().view(np.uint32)[idx], bo), k
+    finally:
+        for j in jobs:
+            j["code"].close()
+
+
+def test_batch_grouped_qc_frame_fills_block(fwbf):
+    """The grouped kernel with a QC N=16384 job: one of its frames fills a
+    block's shared memory, so all 16 warps of the block decode it; beside an
+    EG(1023,781) job (two warps per frame).  Both jobs equal fwbf_decode."""
+    specs = [(make_code("qc16384"), 32, 40, 5.5), (make_code("eg1023"), 31, 96, 3.5)]
+    jobs = []
+    try:
+        for i, (h, p, F, eb) in enumerate(specs):
+            c = np.zeros((F, h.N), dtype=np.uint8)
+            q = oracle.quantize(bpsk_awgn(c, eb, max(0.5, 1.0 - h.M / h.N), seed=90 + i))
+            jobs.append(dict(qd=torch.from_numpy(q).cuda(), code=fwbf.Code.from_parity_check(h, p)))
+        outs = [j["code"].outputs(j["qd"].shape[0]) for j in jobs]
+        spec = [(j["code"].handle, j["qd"], 40, 1.5, b, it) for j, (b, it) in zip(jobs, outs)]
+        batch = fwbf.fwbf_batch_create(spec, warps_per_cta=16, packed=2)
+        try:
+            qc, eg = fwbf.fwbf_batch_query(batch, 0), fwbf.fwbf_batch_query(batch, 1)
+            assert qc.grouped == 1 and eg.grouped == 1
+            assert (qc.decoder, qc.warps_per_frame, qc.frames_per_cta) == (fwbf.FWBF_DECODER_QC, 16, 1)
+            assert (eg.decoder, eg.warps_per_frame) == (fwbf.FWBF_DECODER_CYCLIC, 2)
+            fwbf.fwbf_decode_batch(batch)
+            torch.cuda.synchronize()
+            assert fwbf.fwbf_batch_status() == 0
+        finally:
+            fwbf.fwbf_batch_destroy(batch)
+        for k, (j, (b, it)) in enumerate(zip(jobs, outs)):
+            sb, si = j["code"].decode(j["qd"], 40, 1.5)
+            torch.cuda.synchronize()
+            assert torch.equal(it, si) and torch.equal(b, sb), k
     finally:
         for j in jobs:
             j["code"].close()
