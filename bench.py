@@ -44,8 +44,10 @@ WORKLOAD = dict(code="eg1023", ebn0_db=4.0, frames=1 << 20, max_iter=100, seg_le
 # DRAM bytes (read + write) per frame of each decode kernel, from one ncu
 # capture of that kernel on 131,072 frames of this workload (traffic is the
 # frame bytes in and the decisions out, so it scales with frames); None when
-# the kernel has changed since the capture.
-TRAFFIC_BYTES_PER_FRAME = {"plain": None, "learned": None}
+# the kernel has changed since the capture.  The capture's command and figures
+# are in profiles/ (fwbf_decode_kernels_eg1023_4dB.md).
+TRAFFIC_BYTES_PER_FRAME = {"plain": (134.136832e6 + 7.947264e6) / 131072,    # 1,084 B
+                           "learned": (134.182656e6 + 8.307456e6) / 131072}  # 1,087 B
 NETWORK_FLOPS_PER_EVAL = 2 * (8 * 64 + 64 * 64 + 64 * 2)  # multiply-adds of 8 -> 64 -> 64 -> 2, x2
 
 

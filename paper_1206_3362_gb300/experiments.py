@@ -19,6 +19,10 @@
   one launch per code and point) on the same frames.  Frames reuse a pool of
   seeded codewords under fresh seeded noise (FWBF's outcome depends only on the
   error pattern and |y|, not on which codeword was sent).
+* ``kernels``: one launch of each benchmarked decode kernel on 131,072
+  EG(1023,781) frames at 4 dB (134 MB of int8 frames, more than L2): plain
+  FWBF in the paper setting (p = 31, alpha = 1.5) and the learned + batched
+  form (p = 8, alpha 2, gate 14 d_v); a small case for profilers.
 * ``qc``: plain FWBF (paper setting) on the quasi-cyclic N = 16384 and
   N = 8192 codes at 4 dB: the packed quasi-cyclic decoder, and the list decoder
   on the same code with its checks (rows) permuted -- no circulant structure
@@ -30,6 +34,7 @@
     python -m paper_1206_3362_gb300.experiments scale4 [--frames N]
     python -m paper_1206_3362_gb300.experiments sweep1 [--frames N]
     python -m paper_1206_3362_gb300.experiments qc [--frames N]
+    python -m paper_1206_3362_gb300.experiments kernels [--frames N]
 """
 from __future__ import annotations
 
@@ -342,6 +347,37 @@ def qc_decoders(frames: int = 1 << 16, reps: int = 3, ebn0: float = 4.0, max_ite
     return out
 
 
+def kernels(frames: int = 1 << 17, gate_dv: int = 14):
+    """One plain FWBF decode (p = 31, alpha = 1.5) and one graph-free
+    learned + batched launch (the committed network, its p and alpha, gate
+    gate_dv) of the same seeded frames; returns their failure counts."""
+    import torch
+
+    from .inputs import Encoder, make_code
+    from .inputs.channel import bpsk_awgn_torch, random_codewords_torch
+    from .learned import DEFAULT_WEIGHTS, Network
+
+    h = make_code("eg1023")
+    enc = Encoder(h)
+    _, c = random_codewords_torch(enc, frames, seed=7, device="cuda")
+    q = fwbf.quantize(bpsk_awgn_torch(c, 4.0, enc.rate, seed=7).contiguous())
+    net = Network(alpha_default=2.0)
+    meta = net.load(DEFAULT_WEIGHTS)
+    p_l, a_l, k_l = int(meta["seg_len"]), float(meta["alpha_default"]), int(meta["k_learn"])
+    with fwbf.Code.from_parity_check(h, 31) as code31, fwbf.Code.from_parity_check(h, p_l) as code_l:
+        b31, i31 = code31.outputs(frames)
+        fwbf.fwbf_decode(code31.handle, q, 100, 1.5, b31, i31)
+        bl, il = code_l.outputs(frames)
+        batch = fwbf.fwbf_batch_create([(code_l.handle, q, 100, a_l, bl, il, net.blob, k_l, gate_dv)],
+                                       warps_per_cta=16, packed=2)
+        try:
+            fwbf.fwbf_decode_batch(batch)
+            torch.cuda.synchronize()
+        finally:
+            fwbf.fwbf_batch_destroy(batch)
+        return {"frames": frames, "plain_failed": int((i31 < 0).sum()), "learned_failed": int((il < 0).sum())}
+
+
 def main():
     import argparse
 
@@ -350,7 +386,7 @@ def main():
     import __graft_entry__
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["tab1", "eg255", "scale4", "sweep1", "qc"])
+    ap.add_argument("what", choices=["tab1", "eg255", "scale4", "sweep1", "qc", "kernels"])
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
@@ -364,6 +400,8 @@ def main():
         res = sweep1(args.frames or (1 << 20))
     elif args.what == "qc":
         res = qc_decoders(args.frames or (1 << 16))
+    elif args.what == "kernels":
+        res = kernels(args.frames or (1 << 17))
     else:
         res = scale4(args.frames or (1 << 22))
     text = json.dumps(res, indent=1)
