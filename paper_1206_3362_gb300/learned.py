@@ -358,7 +358,10 @@ def main():
     ap.add_argument("--report", default=None)
     ap.add_argument("--weights", default=None, help="evaluate these weights instead of training")
     ap.add_argument("--oversample", type=int, default=1, help="repeat non-default labels this many times")
+    ap.add_argument("--gate-dv", default="6",
+                    help="comma-separated gates: the network runs on passes with W_k >= gate * d_v")
     args = ap.parse_args()
+    gates = tuple(int(x) for x in args.gate_dv.split(","))
     torch.cuda.set_device(0)
     h = make_code(args.code)
     enc = Encoder(h)
@@ -387,9 +390,12 @@ def main():
     code31 = fwbf.Code.from_parity_check(h, args.p_ref)
     for eb in ebn0:
         q, c = make_frames(code, enc, args.eval_frames, (eb,), seed=777, device="cuda")
-        res[f"{eb}dB"] = {f"plain_p{args.p_ref}": evaluate(code31, q, c, None, paper),
-                          "plain_tuned": evaluate(code, q, c, None, sch),
-                          "learned_batched": evaluate_batched(code, q, c, net, sch)}
+        point = {f"plain_p{args.p_ref}": evaluate(code31, q, c, None, paper),
+                 "plain_tuned": evaluate(code, q, c, None, sch)}
+        for g in gates:
+            key = "learned_batched" if len(gates) == 1 else f"learned_batched_g{g}"
+            point[key] = evaluate_batched(code, q, c, net, dataclasses.replace(sch, gate_dv=g))
+        res[f"{eb}dB"] = point
         print(json.dumps({f"{eb}dB": res[f"{eb}dB"]}), flush=True)
     if args.report:
         with open(args.report, "w") as f:
