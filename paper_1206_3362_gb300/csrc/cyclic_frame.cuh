@@ -85,6 +85,27 @@ __device__ __forceinline__ void build_doubled(uint32_t *X2, int Z, int H, int XJ
     for (int j = Z + t; j < XJ; j += G) X2[j] = v(j - Z) | (v(j - zh) << 16);
 }
 
+// Writes a = v(i) and b = v(i + H) (pair i < H; b only if i + H < Z) into every
+// half-word of the doubled array that holds them.  v(x) is the low half of
+// words x and x + Z, the high half of words (x - H) mod Z and that + Z (each
+// while < XJ); for pair i that is: words i and i + Z (i < H - 1) whole, the low
+// half of word i + H and the high half of word i + Z - H.  Over all pairs the
+// whole-word stores ([0, H - 1) or [0, H), and [Z, XJ)) and the half-word
+// stores ([Z - H, Z)) touch disjoint words, so no two stores overlap.
+__device__ __forceinline__ void doubled_pair_store(uint32_t *X2, int i, uint32_t a, uint32_t b, bool has_b, int Z,
+                                                   int H) {
+    uint16_t *X16 = reinterpret_cast<uint16_t *>(X2);
+    if (has_b) {
+        const uint32_t w = a | (b << 16);
+        X2[i] = w;
+        if (i < H - 1) X2[i + Z] = w;
+        X16[2 * (i + H)] = (uint16_t)b;
+    } else {
+        X16[2 * i] = (uint16_t)a;  // the high half is v(0), stored by pair 0
+    }
+    X16[2 * (i + Z - H) + 1] = (uint16_t)a;
+}
+
 // Adds delta to every half-word of the doubled array that holds position m
 // (after all updates of a pass the half-words are back in [1, 255]; the
 // additions commute, so updates of several flips may interleave).
@@ -229,14 +250,20 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     }
     int iters = 0, mode = VAR == kVarPlain ? kModePlain : VAR == kVarLearned ? kModeLearned : P.mode;
     for (;;) {  // attempts: the requested mode, then plain FWBF as fallback
-    for (int i = t; i < H; i += G) SC[i] = 0x40004000u;
-
-    for (int w = gw; w < Zw; w += WPF) {
-        const int n = (w << 5) + lane;
-        const uint32_t zb = __ballot_sync(FULL, n < Z && q[n] < 0);
-        if (lane == 0) zbits[w] = zb;
+    // per pair i (a warp's 32 pairs lie in one 32-bit word of decisions, as
+    // H % 32 == 0): the check keys of both positions into the doubled array,
+    // the hard decisions, the cleared corrections
+    for (int i = t; i < H; i += G) {
+        const bool has_b = i + H < Z;
+        const int qa = q[i], qb = has_b ? q[i + H] : 0;
+        doubled_pair_store(X2, i, qkey(qa), qkey(qb), has_b, Z, H);
+        SC[i] = 0x40004000u;
+        const uint32_t za = __ballot_sync(FULL, qa < 0), zb = __ballot_sync(FULL, qb < 0);
+        if (lane == 0) {
+            zbits[i >> 5] = za;
+            zbits[(i + H) >> 5] = zb;  // (i + H < Z for lane 0: Z >= 2H - 1)
+        }
     }
-    build_doubled(X2, Z, H, XJ, t, G, [&](int n) { return qkey(q[n]); });
     group_sync<WPF>(bar_id);
 
     // ---- check pass: min1/pos, min2 and parity of every check pair; the
@@ -310,7 +337,9 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                 const uint32_t diff = min2 - min1;
                 int n = m + (int)d_off[pos];
                 n = n >= Z ? n - Z : n;
-                crec[m] = min1 | (diff << 8) | ((uint32_t)n << 16);  // min1, diff, arg-min bit
+                // min1, the syndrome bit at the check pass (read only by the V'
+                // build below), diff, arg-min bit
+                crec[m] = min1 | ((half ? s_hi : s_lo) << 7) | (diff << 8) | ((uint32_t)n << 16);
                 if (diff) {
                     int idx, sh;
                     pair_slot(n, H, idx, sh);
@@ -332,10 +361,13 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     if constexpr (WPF == 1) __syncwarp();
 
     // the doubled array of V'_m = (2 s_m - 1) min1_m + 128, kept current
-    build_doubled(X2, Z, H, XJ, t, G, [&](int n) {
-        const uint32_t mn = crec[n] & 0x7fu;
-        return ((sbits[n >> 5] >> (n & 31)) & 1u) ? 128u + mn : 128u - mn;
-    });
+    for (int i = t; i < H; i += G) {
+        const bool has_b = i + H < Z;
+        const uint32_t ra = crec[i], rb = has_b ? crec[i + H] : 0u;
+        const uint32_t va = (ra & 0x80u) ? 128u + (ra & 0x7fu) : 128u - (ra & 0x7fu);
+        const uint32_t vb = (rb & 0x80u) ? 128u + (rb & 0x7fu) : 128u - (rb & 0x7fu);
+        doubled_pair_store(X2, i, va, vb, has_b, Z, H);
+    }
     group_sync<WPF>(bar_id);
 
     // ---- iterations ------------------------------------------------------
