@@ -459,7 +459,7 @@ def main():
         "bound": "alu", "achieved": ach_l, "peak": peak, "unit": "Tops/s", "frac": ach_l / peak,
         "traffic": (TRAFFIC_BYTES_PER_FRAME["learned"] * F if TRAFFIC_BYTES_PER_FRAME["learned"] else None),
         "algorithmic_bytes": F * (N + 4 * ((N + 31) // 32) + 4),
-        "kernel": "fwbf_decode_batch_kernel<true, true> (learned job)", "decode_ms": dec_l,
+        "kernel": "fwbf_decode_batch_kernel<true, true, true, 2> (one learned job)", "decode_ms": dec_l,
         "ops_basis": "method integer ops (init 2E+N per frame, 2E+N+B per pass, failures at K_max) + "
                      f"{NETWORK_FLOPS_PER_EVAL} flops per network evaluation",
         "peak_basis": plain_roofline["peak_basis"], "peak_measured": peak_meas,

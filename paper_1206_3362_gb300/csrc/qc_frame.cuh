@@ -15,8 +15,11 @@
 //   * per pass: V'_m = (2 s_m - 1) min1_m + 128 lives in a doubled pair array
 //     per block row (X2r[k] = V'(r, k mod Z) | V'(r, (k + H) mod Z) << 16), so
 //     a bit pair gathers over its column's entries (r, t') with one aligned,
-//     conflict-free load each: D_n = G_n - 128 d_v(c) + SC_n - 0x4000, metric
-//     E' = 256 D_n - alpha_q |q_n|.
+//     conflict-free load each: D_n = G_n - 128 d_v(c) + SC_n + T_n - 0x8000,
+//     metric E' = 256 D_n - alpha_q |q_n|.  SC holds the corrections less the
+//     frame-constant T_n = floor((alpha_q |q_n| + theta_q) / 256) (capped at
+//     127 * 127, above any D_n): E' > theta_q iff D_n - T_n >= 1, so one packed
+//     test per bit pair selects exactly the candidates.
 //   * flips toggle the syndrome and keep V' and SC current with atomics; a
 //     pass without flips ends the frame (its state would repeat to K_max).
 #pragma once
@@ -63,7 +66,7 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
     int8_t *stage = reinterpret_cast<int8_t *>(ws);
     uint32_t *X2 = reinterpret_cast<uint32_t *>(ws + P.off_X);
     uint32_t *crec = reinterpret_cast<uint32_t *>(ws + P.off_crec);
-    uint32_t *SC = reinterpret_cast<uint32_t *>(ws + P.off_SC);  // per bit pair, halves biased by 0x4000
+    uint32_t *SC = reinterpret_cast<uint32_t *>(ws + P.off_SC);  // per bit pair, halves biased by 0x8000
     uint32_t *sbits = reinterpret_cast<uint32_t *>(ws + P.off_s);
     uint32_t *zbits = reinterpret_cast<uint32_t *>(ws + P.off_z);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
@@ -95,7 +98,6 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
         }
         *reinterpret_cast<uint4 *>(stage + c * 16) = clamp_m127(v);  // -128 decodes as -127
     }
-    for (int i = t; i < NB * (int)H; i += G) SC[i] = 0x40004000u;
     group_sync<WPF>(bar_id);
     // the staged bytes become sign-magnitude bytes sm = |q| << 1 | (q < 0),
     // four per word (per byte: |q| = (q ^ 0xff) + 1 for q < 0, no carry
@@ -115,6 +117,22 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
         const uint32_t zb = __ballot_sync(FULL, sm[n] & 1u);
         if (lane == 0) zbits[w] = zb;
     }
+    // corrections of bit pair (c, j), (c, j + H): 0x8000 - T_n per half, T_n
+    // capped at 127 * 127 (|SC_n| <= 127 d_v and |D_n| <= 127 d_v, d_v <= 127:
+    // a half stays in [510, 65025] and the pass's packed test exact)
+    {
+        const uint32_t aq = (uint32_t)P.alpha_q, tq = (uint32_t)P.theta_q;
+        auto tn = [&](uint32_t n) {
+            const uint32_t v = (aq * (uint32_t)(sm[n] >> 1) + tq) >> 8;
+            return v < 16129u ? v : 16129u;
+        };
+        for (int i = t; i < NB * (int)H; i += G) {
+            const uint32_t c = div_small((uint32_t)i, H, P.h_magic);
+            const uint32_t n = c * Z + ((uint32_t)i - c * H);
+            SC[i] = 0x80008000u - (tn(n) | (tn(n + H) << 16));
+        }
+    }
+    group_sync<WPF>(bar_id);  // (the check pass adds into any pair's corrections)
 
     // ---- check pass: check pairs (r, i), (r, i + H); a warp's 32 lanes take
     //      32 consecutive i of one block row (H is a multiple of 32) -----------
@@ -195,13 +213,17 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
         // chunks of 32 R consecutive pairs of one block column, R per lane
         // (the column's entries and addresses shared by the lane's R pairs)
         const int cpc = (int)H / (32 * R);  // chunks per block column
+        // chunk ch = c * cpc + k of this warp, (c, k) stepped along with ch
+        int cc = 0, ck = gw;
+        while (ck >= cpc) ck -= cpc, ++cc;
         for (int ch = gw; ch < NB * cpc; ch += WPF) {
-            const uint32_t c = (uint32_t)(ch / cpc);
-            const uint32_t j0 = (uint32_t)(ch - (int)c * cpc) * 32u * R + (uint32_t)lane;
-            // D_n = G_n - 128 d_v(c) + SC_n - 0x4000: the block column's own
-            // weight d_v(c) (block columns may differ in weight)
+            const uint32_t c = (uint32_t)cc;
+            const uint32_t j0 = (uint32_t)ck * 32u * R + (uint32_t)lane;
+            for (ck += WPF; ck >= cpc; ck -= cpc) ++cc;
+            // D_n - T_n = G_n - 128 d_v(c) + SC_n - 0x8000: the block column's
+            // own weight d_v(c) (block columns may differ in weight)
             const uint32_t e0 = cptr[c], e1 = cptr[c + 1];
-            const int bias = 128 * (int)(e1 - e0) + 0x4000;
+            const int bias = 128 * (int)(e1 - e0) + 0x8000;
             const uint32_t dfilter = (uint32_t)(0x8000 - bias - 1) * 0x10001u;
             uint32_t acc[R];
 #pragma unroll
@@ -216,7 +238,9 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
             for (int r = 0; r < R; ++r) {
                 const uint32_t j = j0 + 32u * r;
                 const uint32_t SC2 = SC[c * H + j];
-                // D_n >= 1 is necessary for E' > theta >= 0 (both halves at once)
+                // D_n - T_n >= 1, i.e. E' > theta: both halves at once (per half
+                // 0x8000 + D_n - T_n - 1 in [0, 65535], so the 32-bit sum is the
+                // packed pair exactly)
                 const uint32_t cmask = (acc[r] + SC2 + dfilter) & 0x80008000u;
                 if (cmask == 0u) continue;
 #pragma unroll
@@ -224,7 +248,9 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
                     const uint32_t n = c * Z + j + (half ? H : 0u);
                     const int Gv = (int)((acc[r] >> (16 * half)) & 0xffffu);
                     const int sc = (int)((SC2 >> (16 * half)) & 0xffffu);
-                    const int E = (Gv + sc - bias) * 256 - aq * (int)(sm[n] >> 1);
+                    const int a = (int)(sm[n] >> 1);
+                    const uint32_t tnv = ((uint32_t)aq * (uint32_t)a + (uint32_t)tq) >> 8;
+                    const int E = (Gv + sc - bias + (int)(tnv < 16129u ? tnv : 16129u)) * 256 - aq * a;
                     if (E > tq) {
                         const uint32_t blk = div_small(n, P.p, P.p_magic);
                         const unsigned long long key =
