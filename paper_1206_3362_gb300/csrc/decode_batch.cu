@@ -110,13 +110,19 @@ __device__ __forceinline__ void batch_qc_groups(const BatchJob &J, const uint32_
     unsigned char *ws = smem + J.table_smem_bytes + grp * J.warp_bytes;
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + J.qp.off_keys);
     for (int b = t; b < J.qp.B; b += G) keys[b] = 0ull;
+    qc_group_init<WPF>(J.qp, ws, t);
+    uint32_t lpar = 0;  // phase of the group's frame-load mbarrier
     for (;;) {
         if (t == 0) fslot[grp] = atomicAdd(J.counter, 1ull);
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];
         if (f >= (unsigned long long)J.F) break;
-        qc_frame<R, WPF>(J.qp, tbl, ws, t, bar_id, f);
+        if (!qc_frame<R, WPF>(J.qp, tbl, ws, t, bar_id, f, lpar)) {
+            if (t == 0) atomicOr(&g_status_batch, 2);
+            return;  // (the frame's copy did not arrive: the group leaves)
+        }
     }
+    qc_group_done(J.qp, ws, t);
 }
 
 template <int WPF>

@@ -31,13 +31,19 @@ __global__ void __launch_bounds__(768, 1) fwbf_decode_i8_qc_kernel(const __grid_
     unsigned char *ws = smem + P.table_smem_bytes + grp * P.warp_bytes;
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(ws + P.off_keys);
     for (int b = t; b < P.B; b += G) keys[b] = 0ull;
+    qc_group_init<WPF>(P, ws, t);
+    uint32_t lpar = 0;  // phase of the group's frame-load mbarrier
     for (;;) {
         if (t == 0) fslot[grp] = atomicAdd(P.counter, 1ull);
         group_sync<WPF>(bar_id);
         const unsigned long long f = fslot[grp];  // rewritten only after the frame's last meeting
         if (f >= (unsigned long long)P.F) break;
-        qc_frame<R, WPF>(P, st, ws, t, bar_id, f);
+        if (!qc_frame<R, WPF>(P, st, ws, t, bar_id, f, lpar)) {
+            if (t == 0) atomicOr(&g_status_i8_qc, 2);
+            return;  // (the frame's copy did not arrive: the group leaves)
+        }
     }
+    qc_group_done(P, ws, t);
 }
 
 constexpr uint32_t kQcReserve = 1024u;  // static shared memory of the kernel

@@ -41,8 +41,25 @@ struct QcParams {
     uint32_t *out_bits;
     int32_t *out_iters;
     unsigned long long *counter;
-    uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys, off_red;
+    uint32_t warp_bytes, off_X, off_crec, off_SC, off_s, off_z, off_keys, off_mbar, off_red;
+    int lane_shift; // 2^lane_shift lanes per flipped bit: the largest column weight, up to 32
 };
+
+// Before a group's first frame: its frame-load mbarrier (thread t == 0; the
+// group meets before the first wait) and its load-timeout flag.
+template <int WPF>
+__device__ __forceinline__ void qc_group_init(const QcParams &P, unsigned char *ws, int t) {
+    if (t == 0) {
+        mbar_init(reinterpret_cast<uint64_t *>(ws + P.off_mbar), 1);
+        *reinterpret_cast<int *>(ws + P.off_mbar + 8) = 0;
+    }
+}
+
+// After a group's last frame (every copy waited for): ends its mbarrier, whose
+// shared memory the block may use for another job's slices.
+__device__ __forceinline__ void qc_group_done(const QcParams &P, unsigned char *ws, int t) {
+    if (t == 0) mbar_inval(reinterpret_cast<uint64_t *>(ws + P.off_mbar));
+}
 
 // arg-min correction slot of bit (c, a): pair word c * H + (a mod H), half a >= H
 __device__ __forceinline__ void qc_pair_slot(uint32_t c, uint32_t a, uint32_t H, uint32_t &idx, uint32_t &shift) {
@@ -54,9 +71,11 @@ __device__ __forceinline__ void qc_pair_slot(uint32_t c, uint32_t a, uint32_t H,
 // Decodes frame f of P with a group of WPF warps (thread t of 32 * WPF); tbl
 // is the code's table blob staged in shared memory, ws the group's slice,
 // bar_id its named barrier (WPF > 1).
+// Returns false (for every thread of the group) if the frame's bulk copy did
+// not arrive within the wait limit; lpar is the group's mbarrier phase.
 template <int R, int WPF>  // pairs per lane per gather chunk, warps per frame
-__device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl, unsigned char *ws, int t, int bar_id,
-                                         unsigned long long f) {
+__device__ __forceinline__ bool qc_frame(const QcParams &P, const uint32_t *tbl, unsigned char *ws, int t, int bar_id,
+                                         unsigned long long f, uint32_t &lpar) {
     constexpr int G = 32 * WPF;
     const int lane = t & 31, gw = t >> 5;
     const uint32_t *rptr = tbl + P.rptr_off;
@@ -77,41 +96,46 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
     const int N = NB * (int)Z;
     const int Nw = N >> 5;
     const uintptr_t ybase = reinterpret_cast<uintptr_t>(P.y);
-    const uintptr_t yend = ybase + (uintptr_t)(P.F * (int64_t)N);
 
-    // ---- frame load (aligned 16-byte chunks; byte loads at the buffer end)
+    // ---- frame load: one bulk copy (TMA) of the frame's N bytes (y is
+    // 16-byte aligned and N a multiple of 64), thread t == 0 issuing it and
+    // the group waiting on its mbarrier (bounded)
     const uintptr_t fb = ybase + (uintptr_t)(f * (unsigned long long)N);
-    const uintptr_t a0 = fb & ~(uintptr_t)15;
-    const int off = (int)(fb - a0);
-    const int nchunks = (off + N + 15) >> 4;
-    for (int c = t; c < nchunks; c += G) {
-        const uintptr_t src = a0 + (uintptr_t)c * 16;
-        uint4 v;
-        if (src + 16 <= yend) {
-            v = __ldcs(reinterpret_cast<const uint4 *>(src));
-        } else {
-            uint32_t wv[4] = {0u, 0u, 0u, 0u};
-            for (int i = 0; i < 16; ++i)
-                if (src + i < yend)
-                    wv[i >> 2] |= (uint32_t)(*reinterpret_cast<const unsigned char *>(src + i)) << (8 * (i & 3));
-            v = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    const int nwords = N >> 2;
+    int *lflag = reinterpret_cast<int *>(ws + P.off_mbar + 8);
+    {
+        uint64_t *mbar = reinterpret_cast<uint64_t *>(ws + P.off_mbar);
+        if (t == 0) {
+            // the previous frame's generic-proxy accesses of the stage (ordered
+            // before this thread by the group's last meeting) before the copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(mbar, (uint32_t)N);
+            for (uint32_t o = 0; o < (uint32_t)N; o += kBulkChunk)
+                bulk_g2s(stage + o, reinterpret_cast<const void *>(fb + o),
+                         (uint32_t)N - o < kBulkChunk ? (uint32_t)N - o : kBulkChunk, mbar);
         }
-        *reinterpret_cast<uint4 *>(stage + c * 16) = clamp_m127(v);  // -128 decodes as -127
+        if (!mbar_wait_bounded(mbar, lpar, kWaitLimitNs)) {
+            mbar_wait_bounded(mbar, lpar, kWaitLimitNs);  // let a late copy land before leaving
+            atomicOr(lflag, 1);
+        }
+        lpar ^= 1u;
     }
     group_sync<WPF>(bar_id);
+    if (*lflag) return false;  // (read by every thread after the meeting)
     // the staged bytes become sign-magnitude bytes sm = |q| << 1 | (q < 0),
-    // four per word (per byte: |q| = (q ^ 0xff) + 1 for q < 0, no carry
-    // across bytes since |q| <= 127); sm << 7 is the packed check-pass key
+    // four per word, -128 read as -127 (per byte: |q| = (q ^ 0xff) + 1 for
+    // q < 0, no carry across bytes since |q| <= 127); sm << 7 is the packed
+    // check-pass key
     {
         uint32_t *w32 = reinterpret_cast<uint32_t *>(stage);
-        for (int w = t; w < nchunks * 4; w += G) {
-            const uint32_t x = w32[w];
+        for (int w = t; w < nwords; w += G) {
+            const uint32_t x = __vmaxs4(w32[w], 0x81818181u);
             const uint32_t sg = (x >> 7) & 0x01010101u;
             w32[w] = (((x ^ (sg * 0xffu)) + sg) << 1) | sg;
         }
     }
     group_sync<WPF>(bar_id);
-    const uint8_t *sm = reinterpret_cast<const uint8_t *>(stage) + off;
+    const uint8_t *sm = reinterpret_cast<const uint8_t *>(stage);
     for (int w = gw; w < Nw; w += WPF) {
         const int n = (w << 5) + lane;
         const uint32_t zb = __ballot_sync(FULL, sm[n] & 1u);
@@ -261,41 +285,59 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
             }
         }
         group_sync<WPF>(bar_id);
-        // flips: a thread per block; the flipped bit's checks one after another
+        // flips: warp gw reads the keys of 32 blocks at a time (b = b0 + lane);
+        // the flipped bits' positions go, in lane order, into the slots of
+        // those keys (read, so free), and 2^lsh lanes per flipped bit then
+        // update its checks (the column's entries e = lane mod 2^lsh, stepping
+        // by 2^lsh): 32 >> lsh flipped bits per step, every update by atomics
         int dW = 0, nflip = 0;
-        for (int b = t; b < P.B; b += G) {
-            const unsigned long long key = keys[b];
-            if (!key) continue;
-            keys[b] = 0ull;
-            ++nflip;
-            const uint32_t n = 0xffffffffu - (uint32_t)key;
-            atomicXor(&zbits[n >> 5], 1u << (n & 31));
-            const uint32_t c = div_small(n, Z, P.z_magic);
-            const uint32_t j = n - c * Z;
-            for (uint32_t e = cptr[c]; e < cptr[c + 1]; ++e) {
-                const uint32_t ent = cent[e];
-                const uint32_t r = ent >> 16;
-                uint32_t a = j + (ent & 0xffffu);
-                a = a >= Z ? a - Z : a;
-                const uint32_t m = r * Z + a;
-                const uint32_t bit = 1u << (m & 31);
-                const uint32_t old = atomicXor(&sbits[m >> 5], bit);
-                const bool now_set = !(old & bit);
-                dW += now_set ? 1 : -1;
-                const uint32_t rec = crec[m];
-                const int min1 = (int)(rec & 0x7fu), diff = (int)((rec >> 8) & 0x7fu);
-                doubled_add(X2 + r * XJ, (int)a, now_set ? 2 * min1 : -2 * min1, (int)Z, (int)H, XJ);
-                if (diff) {
-                    const uint32_t na = rec >> 16;
-                    const uint32_t ca = div_small(na, Z, P.z_magic);
-                    uint32_t idx, sh;
-                    qc_pair_slot(ca, na - ca * Z, H, idx, sh);
-                    const int d = now_set ? 2 * diff : -2 * diff;
-                    atomicAdd(&SC[idx], (uint32_t)d << sh);
+        const int lsh = P.lane_shift, lpf = 1 << lsh;
+        for (int b0 = 32 * gw; b0 < P.B; b0 += G) {
+            const int b = b0 + lane;
+            const unsigned long long key = b < P.B ? keys[b] : 0ull;
+            const uint32_t pend = __ballot_sync(FULL, key != 0ull);
+            if (pend == 0u) continue;
+            const int nf = __popc(pend);
+            nflip += nf;  // (warp-uniform)
+            uint32_t *slot = reinterpret_cast<uint32_t *>(keys + b0);  // nf < 2 (B - b0) words
+            if (key) {
+                const uint32_t n = 0xffffffffu - (uint32_t)key;
+                atomicXor(&zbits[n >> 5], 1u << (n & 31));
+                slot[__popc(pend & ((1u << lane) - 1u))] = n;  // (after the warp's key reads: the ballot)
+            }
+            __syncwarp();
+            for (int k = lane >> lsh; k < nf; k += 32 >> lsh) {
+                const uint32_t n = slot[k];
+                const uint32_t c = div_small(n, Z, P.z_magic);
+                const uint32_t j = n - c * Z;
+                const uint32_t e1 = cptr[c + 1];
+                for (uint32_t e = cptr[c] + (uint32_t)(lane & (lpf - 1)); e < e1; e += (uint32_t)lpf) {
+                    const uint32_t ent = cent[e];
+                    const uint32_t r = ent >> 16;
+                    uint32_t a = j + (ent & 0xffffu);
+                    a = a >= Z ? a - Z : a;
+                    const uint32_t m = r * Z + a;
+                    const uint32_t bit = 1u << (m & 31);
+                    const uint32_t old = atomicXor(&sbits[m >> 5], bit);
+                    const bool now_set = !(old & bit);
+                    dW += now_set ? 1 : -1;
+                    const uint32_t rec = crec[m];
+                    const int min1 = (int)(rec & 0x7fu), diff = (int)((rec >> 8) & 0x7fu);
+                    doubled_add(X2 + r * XJ, (int)a, now_set ? 2 * min1 : -2 * min1, (int)Z, (int)H, XJ);
+                    if (diff) {
+                        const uint32_t na = rec >> 16;
+                        const uint32_t ca = div_small(na, Z, P.z_magic);
+                        uint32_t idx, sh;
+                        qc_pair_slot(ca, na - ca * Z, H, idx, sh);
+                        const int d = now_set ? 2 * diff : -2 * diff;
+                        atomicAdd(&SC[idx], (uint32_t)d << sh);
+                    }
                 }
             }
+            __syncwarp();
+            if (b < P.B) keys[b] = 0ull;  // the slots and the read keys, for the next pass
         }
-        const int3 tot = group_sum3<WPF>(make_int3(warp_sum(dW), warp_sum(nflip), 0), red, rhalf, lane, gw, bar_id);
+        const int3 tot = group_sum3<WPF>(make_int3(warp_sum(dW), nflip, 0), red, rhalf, lane, gw, bar_id);
         W += tot.x;
         if constexpr (WPF == 1) __syncwarp();
         if (tot.y == 0) {  // fixed point: every later pass repeats this one
@@ -308,6 +350,7 @@ __device__ __forceinline__ void qc_frame(const QcParams &P, const uint32_t *tbl,
     for (int w = t; w < Nw; w += G) __stcs(ob + w, zbits[w]);
     if (t == 0) P.out_iters[f] = iters;
     group_sync<WPF>(bar_id);
+    return true;
 }
 
 inline uint32_t qc_magic(uint32_t d) { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + d - 1) / d); }
@@ -332,6 +375,8 @@ inline void qc_layout(const fwbf_code_s *c, QcParams &P) {
     P.p_magic = c->p_magic;
     P.z_magic = c->z_magic;
     P.h_magic = qc_magic((uint32_t)P.H);
+    P.lane_shift = 0;
+    while ((1 << P.lane_shift) < c->dv_max && P.lane_shift < 5) ++P.lane_shift;
     const uint32_t N = (uint32_t)c->N, M = (uint32_t)c->M;
     uint32_t o = a16(N + 32);
     P.off_X = o;
@@ -346,6 +391,8 @@ inline void qc_layout(const fwbf_code_s *c, QcParams &P) {
     o += a16(N / 8u);
     P.off_keys = o;
     o += a16(8u * (uint32_t)P.B);
+    P.off_mbar = o;  // the frame-load mbarrier (8 bytes) and the load-timeout flag
+    o += 16u;
     P.off_red = o;  // group sums: 2 halves x 4 ints x up to 8 warps (qc_set_wpf: 16)
     P.warp_bytes = o + 256u;
 }
