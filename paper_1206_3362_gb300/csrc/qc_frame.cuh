@@ -7,11 +7,12 @@
 //   * bit n = (block column c, j), check m = (block row r, i); positions j and
 //     j + H (H = Z/2) of a block column, and checks i and i + H of a block
 //     row, share one 32-bit word (two 16-bit halves).
-//   * check pass (once per frame): for every check pair, over the row's
-//     entries (c, t) -- bits (c, (i + t) mod Z) -- the packed key
-//     |q| << 8 | sign << 7 | entry gives min1 / arg-min and min2 by packed
-//     min/max, the sign bits the parity; records crec[m] = min1 | diff << 8 |
-//     arg-min bit << 16, and the signed arg-min corrections per bit in SC.
+//   * check pass (once per frame): for four consecutive checks i .. i + 3 of
+//     a block row at once, over the row's entries (c, t) -- bits
+//     (c, (i + t) mod Z) .. -- the packed key |q| << 8 | sign << 7 | entry
+//     gives min1 / arg-min and min2 by packed min/max, the sign bits the
+//     parity; records crec[m] = min1 | diff << 8 | arg-min bit << 16, and the
+//     signed arg-min corrections per bit in SC.
 //   * per pass: V'_m = (2 s_m - 1) min1_m + 128 lives in a doubled pair array
 //     per block row (X2r[k] = V'(r, k mod Z) | V'(r, (k + H) mod Z) << 16), so
 //     a bit pair gathers over its column's entries (r, t') with one aligned,
@@ -158,54 +159,79 @@ __device__ __forceinline__ bool qc_frame(const QcParams &P, const uint32_t *tbl,
     }
     group_sync<WPF>(bar_id);  // (the check pass adds into any pair's corrections)
 
-    // ---- check pass: check pairs (r, i), (r, i + H); a warp's 32 lanes take
-    //      32 consecutive i of one block row (H is a multiple of 32) -----------
+    // ---- check pass: a lane takes four consecutive checks 4 qd .. 4 qd + 3
+    //      of block row r (a warp 32 consecutive quads of one row).  For a
+    //      row entry (c, t) their bits are the four bytes at (4 qd + t) mod Z
+    //      of column c's sign-magnitude bytes: two aligned words of the
+    //      column, funnel-shifted by (t mod 4) bytes, give all four; byte
+    //      permutes spread them over two packed key pairs ----------------------
     int W = 0;
-    for (int pi = t; pi < MB * (int)H; pi += G) {
-        const uint32_t r = div_small((uint32_t)pi, H, P.h_magic);
-        const uint32_t i = (uint32_t)pi - r * H;
-        const uint32_t e0 = rptr[r], e1 = rptr[r + 1];
-        uint32_t k1 = 0xffffffffu, k2 = 0xffffffffu, par = 0u;
-        uint32_t ek = 0u;  // the entry index in both halves
-        for (uint32_t e = e0; e < e1; ++e, ek += 0x10001u) {
-            const uint32_t ent = rent[e];
-            const uint32_t cZ = (ent >> 16) * Z;
-            uint32_t a = i + (ent & 0xffffu);
-            a = a >= Z ? a - Z : a;
-            uint32_t b = a + H;
-            b = b >= Z ? b - Z : b;
-            const uint32_t v = (uint32_t)sm[cZ + a] | ((uint32_t)sm[cZ + b] << 16);
-            const uint32_t key = (v << 7) | ek;  // |q| << 8 | sign << 7 | entry, both halves
-            k2 = vmin_u16x2(k2, vmax_u16x2(k1, key));
-            k1 = vmin_u16x2(k1, key);
-            par ^= v;
-        }
-        const uint32_t s_lo = par & 1u, s_hi = (par >> 16) & 1u;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const uint32_t ii = i + (half ? H : 0u);
-            const uint32_t a1 = k1 >> (16 * half), a2 = k2 >> (16 * half);
-            const uint32_t min1 = (a1 >> 8) & 0x7fu, pos = a1 & 0x7fu, min2 = (a2 >> 8) & 0x7fu;
-            const uint32_t diff = min2 - min1;
-            const uint32_t ent = rent[e0 + pos];
-            const uint32_t c = ent >> 16;
-            uint32_t a = ii + (ent & 0xffffu);
-            a = a >= Z ? a - Z : a;
-            crec[r * Z + ii] = min1 | (diff << 8) | ((c * Z + a) << 16);  // min1, diff, arg-min bit
-            if (diff) {
-                uint32_t idx, sh;
-                qc_pair_slot(c, a, H, idx, sh);
-                const int d = (half ? s_hi : s_lo) ? (int)diff : -(int)diff;
-                atomicAdd(&SC[idx], (uint32_t)d << sh);
+    {
+        const uint32_t Zq = Z >> 2;                  // quads per row (a multiple of 16)
+        const int tpr = (int)((Zq + 31u) >> 5);      // warp tasks per row
+        const uint32_t *w32 = reinterpret_cast<const uint32_t *>(sm);
+        int rr = 0, tk = gw;                         // task = rr * tpr + tk, stepped by WPF
+        while (tk >= tpr) tk -= tpr, ++rr;
+        for (int task = gw; task < MB * tpr; task += WPF) {
+            const uint32_t r = (uint32_t)rr;
+            const uint32_t qd = (uint32_t)tk * 32u + (uint32_t)lane;
+            for (tk += WPF; tk >= tpr; tk -= tpr) ++rr;
+            const bool ok = qd < Zq;                  // (groups of 8 lanes all or none: Zq % 16 == 0)
+            const uint32_t qv = ok ? qd : 0u;
+            const uint32_t e0 = rptr[r], e1 = rptr[r + 1];
+            uint32_t k1a = 0xffffffffu, k2a = 0xffffffffu, k1b = 0xffffffffu, k2b = 0xffffffffu, par = 0u;
+            uint32_t ek = 0u;  // the entry index in both halves
+            for (uint32_t e = e0; e < e1; ++e, ek += 0x10001u) {
+                const uint32_t ent = rent[e];
+                const uint32_t tt = ent & 0xffffu;
+                const uint32_t *col = w32 + (ent >> 16) * Zq;
+                uint32_t wq = qv + (tt >> 2);
+                wq = wq >= Zq ? wq - Zq : wq;
+                const uint32_t wq1 = wq + 1u == Zq ? 0u : wq + 1u;
+                const uint32_t v = __funnelshift_r(col[wq], col[wq1], 8u * (tt & 3u));
+                // |q| << 8 | sign << 7 | entry for checks (0, 1) and (2, 3)
+                const uint32_t ka = __byte_perm(v, 0u, 0x4140) * 128u + ek;
+                const uint32_t kb = __byte_perm(v, 0u, 0x4342) * 128u + ek;
+                k2a = vmin_u16x2(k2a, vmax_u16x2(k1a, ka));
+                k1a = vmin_u16x2(k1a, ka);
+                k2b = vmin_u16x2(k2b, vmax_u16x2(k1b, kb));
+                k1b = vmin_u16x2(k1b, kb);
+                par ^= v;
             }
+            uint32_t nib = 0u;  // the four syndrome bits
+#pragma unroll
+            for (int sidx = 0; sidx < 4; ++sidx) {
+                const uint32_t k1 = sidx < 2 ? k1a : k1b, k2 = sidx < 2 ? k2a : k2b;
+                const uint32_t a1 = k1 >> (16 * (sidx & 1)), a2 = k2 >> (16 * (sidx & 1));
+                const uint32_t min1 = (a1 >> 8) & 0x7fu, pos = a1 & 0x7fu, min2 = (a2 >> 8) & 0x7fu;
+                const uint32_t diff = min2 - min1;
+                const uint32_t sb = (par >> (8 * sidx)) & 1u;
+                nib |= sb << sidx;
+                const uint32_t ii = 4u * qv + (uint32_t)sidx;
+                const uint32_t ent = rent[e0 + pos];
+                const uint32_t c = ent >> 16;
+                uint32_t a = ii + (ent & 0xffffu);
+                a = a >= Z ? a - Z : a;
+                if (ok) {
+                    crec[r * Z + ii] = min1 | (diff << 8) | ((c * Z + a) << 16);  // min1, diff, arg-min bit
+                    if (diff) {
+                        uint32_t idx, sh;
+                        qc_pair_slot(c, a, H, idx, sh);
+                        const int d = sb ? (int)diff : -(int)diff;
+                        atomicAdd(&SC[idx], (uint32_t)d << sh);
+                    }
+                }
+            }
+            if (!ok) nib = 0u;
+            // 8 lanes' nibbles make one 32-bit word of syndrome bits
+            uint32_t wv = nib << (4 * (lane & 7));
+            wv |= __shfl_xor_sync(FULL, wv, 1);
+            wv |= __shfl_xor_sync(FULL, wv, 2);
+            wv |= __shfl_xor_sync(FULL, wv, 4);
+            if (ok && (lane & 7) == 0) sbits[(r * Z + 4u * qv) >> 5] = wv;
+            W += __popc(nib);
         }
-        const uint32_t slo = __ballot_sync(FULL, s_lo);
-        const uint32_t shi = __ballot_sync(FULL, s_hi);
-        if (lane == 0) {
-            sbits[(r * Z + i) >> 5] = slo;
-            sbits[(r * Z + i + H) >> 5] = shi;
-        }
-        W += __popc(slo) + __popc(shi);
+        W = warp_sum(W);  // (per lane so far; the group sum takes lane 0's)
     }
     W = group_sum3<WPF>(make_int3(W, 0, 0), red, rhalf, lane, gw, bar_id).x;  // (meets the group if WPF > 1)
     if constexpr (WPF == 1) __syncwarp();
