@@ -180,10 +180,13 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
     const uintptr_t a0 = fb & ~(uintptr_t)15;
     const int off = (int)(fb - a0);
     const int nchunks = (off + Z + 15) >> 4;
-    // frame statistics for the features of scheduled and learned decoding,
-    // taken from the loaded chunks (bytes outside the frame masked) and summed
-    // over the group with the check pass's syndrome weight
-    const bool stats = VAR == kVarLearned || (VAR == kVarAll && (P.mode != kModePlain || P.out_feat));
+    // frame statistics for the features of scheduled decoding and of recorded
+    // runs, taken from the loaded chunks (bytes outside the frame masked) and
+    // summed over the group with the check pass's syndrome weight; the learned
+    // body takes them from the staged bytes when a pass first consults the
+    // network (about one frame in six at the usual gates: 2.4 % of the frame
+    // time when taken for every frame)
+    const bool stats = VAR == kVarAll && (P.mode != kModePlain || P.out_feat);
     int sa = 0, sw = 0;  // sum of |q_n|, count of |q_n| < 8
     for (int c = t; c < nchunks; c += G) {
         const uintptr_t src = a0 + (uintptr_t)c * 16;
@@ -249,6 +252,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         rhalf = 1;  // half 0 of the group scratch held the statistics
     }
     int iters = 0, mode = VAR == kVarPlain ? kModePlain : VAR == kVarLearned ? kModeLearned : P.mode;
+    bool have_stats = stats;  // fstate[0..1] hold this frame's statistics
     for (;;) {  // attempts: the requested mode, then plain FWBF as fallback
     // per pair i (a warp's 32 pairs lie in one 32-bit word of decisions, as
     // H % 32 == 0): the check keys of both positions into the doubled array,
@@ -357,7 +361,7 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
         }
     }
     W = group_sum3<WPF>(make_int3(W, 0, 0), red, rhalf, lane, gw, bar_id).x;  // (meets the group if WPF > 1)
-    if (stats && t == 0) fstate[2] = (float)W * P.inv_Z;
+    if ((stats || VAR == kVarLearned) && t == 0) fstate[2] = (float)W * P.inv_Z;
     if constexpr (WPF == 1) __syncwarp();
 
     // the doubled array of V'_m = (2 s_m - 1) min1_m + 128, kept current
@@ -415,9 +419,46 @@ __device__ __forceinline__ void cyclic_frame(const CyclicParams &P, const uint32
                     }
                     Wprev = W - dW;
                 }
-                const float4 st = *reinterpret_cast<const float4 *>(fstate);
-                fa = make_float4((float)W * P.inv_Z, (float)Wprev * P.inv_Z, st.z, (float)k * (1.0f / 16.0f));
-                fb = make_float4((float)nflip_prev * P.inv_B, (float)ncand_prev * P.inv_Z, st.x, st.y);
+                float mean_a, weak;
+                if (VAR == kVarLearned && !have_stats) {
+                    // sum |q| and count |q| < 8 over the frame's staged values; the
+                    // group's partial sums pass through the free half of the scratch
+                    // (the other half holds the previous pass's sums read above)
+                    int sa = 0, sw = 0;
+                    for (int n = t; n < Z; n += G) {
+                        const int a = abs((int)q[n]);
+                        sa += a;
+                        sw += a < 8 ? 1 : 0;
+                    }
+                    sa = warp_sum(sa);
+                    sw = warp_sum(sw);
+                    if constexpr (WPF > 1) {
+                        int *r = red + rhalf * 4 * WPF;
+                        if (lane == 0) {
+                            r[4 * gw] = sa;
+                            r[4 * gw + 1] = sw;
+                        }
+                        group_sync<WPF>(bar_id);
+                        sa = sw = 0;
+#pragma unroll
+                        for (int w = 0; w < WPF; ++w) {
+                            sa += r[4 * w];
+                            sw += r[4 * w + 1];
+                        }
+                    }
+                    mean_a = (float)sa / (127.0f * (float)Z);  // (the same arithmetic as at the load)
+                    weak = (float)sw / (float)Z;
+                    if (t == 0) {
+                        fstate[0] = mean_a;
+                        fstate[1] = weak;
+                    }
+                    have_stats = true;
+                } else {
+                    mean_a = fstate[0];
+                    weak = fstate[1];
+                }
+                fa = make_float4((float)W * P.inv_Z, (float)Wprev * P.inv_Z, fstate[2], (float)k * (1.0f / 16.0f));
+                fb = make_float4((float)nflip_prev * P.inv_B, (float)ncand_prev * P.inv_Z, mean_a, weak);
             }
             if (VAR == kVarAll && P.out_feat && k < P.feat_passes && t == 0) {
                 float *o = P.out_feat + (f * (unsigned long long)P.feat_passes + k) * kFeatures;
