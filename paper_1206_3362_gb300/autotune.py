@@ -118,15 +118,22 @@ def select_fastest_qualified(results, ref):
 GATE_CANDIDATES = (0, 6, 10, 12, 14, 16)
 
 
+GATE_TIME_TIE = 0.01  # gates within 1 % of the fastest qualifying one count as equally fast
+
+
 def select_gate(results, plain):
     """The fastest gate whose frame errors are at most the midpoint between
     the ungated network's (gate_dv = 0, which must be measured) and plain
-    FWBF's; the ungated network always qualifies, ties in time keep the
-    earlier entry."""
+    FWBF's; the ungated network always qualifies.  Qualifying gates within
+    GATE_TIME_TIE of the fastest one's time are a tie (their differences are
+    below the timing's run-to-run spread), decided by fewer frame errors, then
+    fewer bit errors, then time, then the earlier entry."""
     full = next(r for r in results if r["gate_dv"] == 0)
     limit = (full["frame_errors"] + plain["frame_errors"]) / 2.0
     qualified = [r for r in results if r is full or r["frame_errors"] <= limit]
-    return min(qualified, key=lambda r: r["ms"])
+    fastest = min(r["ms"] for r in qualified)
+    near = [r for r in qualified if r["ms"] <= fastest * (1.0 + GATE_TIME_TIE)]
+    return min(near, key=lambda r: (r["frame_errors"], r["bit_errors"], r["ms"]))
 
 
 def tune_gate(code, q, c, net, alpha: float, k_learn: int, max_iter: int = 100, candidates=GATE_CANDIDATES,

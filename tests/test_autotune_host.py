@@ -76,3 +76,16 @@ def test_ungated_network_always_qualifies():
     plain = {"frame_errors": 90, "bit_errors": 900, "ms": 10.0}
     results = [_g(0, 100, 12.0), _g(6, 96, 11.0), _g(12, 96, 10.5)]
     assert autotune.select_gate(results, plain) is results[0]
+
+
+def test_gate_near_tie_goes_to_fewer_errors():
+    """Qualifying gates within 1 % of the fastest time (the EG(4095)
+    calibration at 4 dB: every gate within 0.7 %) are a tie decided by frame
+    errors, then bit errors, then time; a gate 1.5 % slower is not in it."""
+    plain = {"frame_errors": 8556, "bit_errors": 673673, "ms": 9.9}
+    results = [_g(0, 5029, 11.10), _g(6, 5029, 11.05), _g(10, 5035, 11.03), _g(12, 5053, 11.028),
+               _g(14, 5073, 11.04), _g(16, 5101, 11.05)]
+    assert autotune.select_gate(results, plain) is results[1]
+    results = [_g(0, 100, 10.20), _g(6, 140, 10.0), _g(12, 150, 10.05)]
+    plain = {"frame_errors": 300, "bit_errors": 3000, "ms": 9.0}
+    assert autotune.select_gate(results, plain) is results[1]
