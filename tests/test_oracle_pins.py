@@ -301,6 +301,28 @@ def test_float_first_metric_single_error():
     assert e0[0, 10] == 16 - 0.5 and iters[0] == 1
 
 
+@pytest.mark.parametrize("key,alpha,theta,A", [("eg15", 1.5, 0.0, 1.0), ("eg15", 0.5, 2.0, 0.75),
+                                                ("eg255", 1.5, 0.0, 0.5), ("eg255", 3.0, 10.0, 2.0)])
+def test_float_margin_single_error_closed_form(key, alpha, theta, A):
+    """The f64 oracle's decision margin, which selects the frames the float32
+    decoder must match, on noiseless y = +-A with one error at j and p = N.
+    Every |y| is A, so every w_{n,m} = A (Eq. 1): the erroneous bit has all d_v
+    checks unsatisfied, E_j = A (d_v - alpha); a bit sharing one check with it
+    (the code has the RC constraint, so at most one) has E = A (2 - d_v - alpha),
+    the largest of the rest.  One pass flips j (E_j > theta) and the next finds
+    the syndrome zero, so the margin is that pass's:
+    min(|E_j - theta|, E_j - A (2 - d_v - alpha)) = min(|A (d_v - alpha) - theta|,
+    A (2 d_v - 2)).  Checked for every error position."""
+    h = make_code(key)
+    dv = int(np.max(h.col_weights()))
+    y = np.full((h.N, h.N), A, dtype=np.float32)
+    y[np.arange(h.N), np.arange(h.N)] = -A
+    bits, iters, margin = oracle.fwbf_f64(h, h.N, y, 5, alpha=alpha, theta=theta)
+    assert (iters == 1).all() and not bits.any()
+    want = min(abs(A * (dv - alpha) - theta), A * (2 * dv - 2))
+    assert np.allclose(margin, want, rtol=0, atol=1e-12), (margin[:4], want)
+
+
 # --------------------------------------------------------------------------
 # statistical band against Tab. 1 (parity unpinned beyond the band)
 # --------------------------------------------------------------------------
